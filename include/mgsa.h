@@ -1,0 +1,165 @@
+/*
+ * mgsa.h - A-orthonormal thin QR by modified Gram-Schmidt on GB300 (sm_103a).
+ *
+ * Computes, for a sparse symmetric positive definite A (m x m, CSR, FP64) and
+ * a tall matrix Z (m x n, m >= n, FP64), the factorization
+ *
+ *     Z = Q R,   Q^T A Q = I_n,   R upper triangular with positive diagonal
+ *
+ * (Imakura & Yamamoto, arXiv 1703.10440, Section 1, eq. (1)), by modified
+ * Gram-Schmidt under the A-inner product (x, y)_A = x^T A y, in one of three
+ * forms (Section 2):
+ *
+ *   MGSA_NAIVE  Algorithms 3/4: two sparse matrix-vector products (MV) per
+ *               column, x_i = A z_i and p_i = A q_i (2n MV in total).
+ *   MGSA_HA     Algorithms 5/7 (high accuracy): one MV per column,
+ *               x_i = A z_i, and p_i = x_i / r_ii (eq. (tec1)), n MV.
+ *   MGSA_HP     Algorithms 6/8 (high performance): one block product X = A Z
+ *               up front; the A-images are carried by the recurrence
+ *               x_j <- x_j - r_ij p_i (eq. (tec2)), p_i = x_i / r_ii.
+ *
+ * All three run right-looking (the row-oriented Algorithms 4, 7, 8): step i
+ * forms r_ii = sqrt(z_i^T x_i), q_i = z_i / r_ii, p_i, the row
+ * r_ij = p_i^T z_j (j > i) and the rank-1 updates z_j <- z_j - r_ij q_i
+ * (and x_j <- x_j - r_ij p_i for HP).  Every step runs in CUDA kernels of this
+ * library; nothing runs on the host but argument checks and launches.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major with a leading dimension (LAPACK style).
+ *   - Pointers named *_dev / in mgsa_csr / Z, Q, R of mgsa_qr are device
+ *     memory owned by the caller; the library never frees them.
+ *   - The library owns its workspace (allocated by mgsa_create and grown by
+ *     mgsa_reserve or by the first call that needs more).
+ *   - Argument errors are detected on the host and returned synchronously,
+ *     before anything is launched.  Numerical failures (breakdown) are
+ *     recorded in a device status word that mgsa_get_info reads.
+ *   - No exception crosses this interface and nothing is printed.
+ *   - A handle is not thread-safe: use one handle per host thread / stream.
+ *   - Results are deterministic: the same inputs, sizes and device give
+ *     bitwise identical Q and R on every call.
+ */
+#ifndef MGSA_H
+#define MGSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t is `struct CUstream_st *`); NULL is the legacy
+ * default stream. */
+typedef struct CUstream_st* mgsa_stream_t;
+
+typedef struct mgsa_context* mgsa_handle;
+
+typedef enum {
+  MGSA_NAIVE = 0, /* Algorithm 4: 2n MV */
+  MGSA_HA = 1,    /* Algorithm 7: n MV, p_i = x_i / r_ii */
+  MGSA_HP = 2     /* Algorithm 8: X = AZ once, x-recurrence */
+} mgsa_variant;
+
+typedef enum {
+  MGSA_OK = 0,
+  MGSA_ERR_INVALID = 1,   /* bad argument; nothing was launched */
+  MGSA_ERR_BREAKDOWN = 2, /* z_j^T x_j <= 0 at some column (A not SPD or Z rank deficient) */
+  MGSA_ERR_NONFINITE = 3, /* z_j^T x_j is NaN or Inf at some column */
+  MGSA_ERR_NOMEM = 4,     /* workspace allocation failed */
+  MGSA_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+  MGSA_ERR_TIMEOUT = 6    /* a device-wide wait gave up (bounded spin); results undefined */
+} mgsa_status;
+
+/* Sparse symmetric positive definite A in CSR form, both triangles stored.
+ * rowptr: m+1 int32, rowptr[0] = 0, non-decreasing, rowptr[m] = nnz.
+ * col:    nnz int32 in [0, m).  val: nnz FP64.
+ * All three arrays are device memory owned by the caller.  Entries of a row
+ * are summed in the order stored. */
+typedef struct {
+  int64_t m;
+  int64_t nnz;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+} mgsa_csr;
+
+/* Largest n accepted by mgsa_qr. */
+#define MGSA_MAX_N 2048
+
+/* Create a handle bound to CUDA device `device`.  Allocates the control block
+ * (status word and device-wide barrier state).  Returns MGSA_ERR_INVALID for a
+ * NULL h or a bad device, MGSA_ERR_NOMEM / MGSA_ERR_CUDA on failure. */
+mgsa_status mgsa_create(mgsa_handle* h, int device);
+
+/* Release every allocation of the handle (synchronizes the device first).
+ * NULL is accepted and ignored. */
+mgsa_status mgsa_destroy(mgsa_handle h);
+
+/* Grow the workspace so that mgsa_qr(m, n, v) allocates nothing; call it
+ * before capturing mgsa_qr into a CUDA graph. */
+mgsa_status mgsa_reserve(mgsa_handle h, int64_t m, int n, mgsa_variant v);
+
+/* Bytes of device workspace mgsa_qr needs for (m, n, v). */
+size_t mgsa_workspace_bytes(mgsa_handle h, int64_t m, int n, mgsa_variant v);
+
+/* A-orthonormal thin QR of Z (Section 1, eq. (1)), right-looking MGS in the
+ * form `v` (Algorithm 4, 7 or 8).
+ *
+ *   A      CSR matrix with A->m == m (device arrays, read only).
+ *   Z      m x n input, column-major, leading dimension ldz >= m (read only).
+ *   Q      m x n output, leading dimension ldq >= m.  Must not overlap Z.
+ *          Q is also the working storage of the z_j^{(i)} columns.
+ *   R      n x n output, leading dimension ldr >= n; written in full, zeros
+ *          below the diagonal.
+ *   s      stream the work is queued on; the call returns without waiting.
+ *
+ * Requirements: 1 <= n <= MGSA_MAX_N, n <= m < 2^31, nnz < 2^31.
+ * Q's columns q_i are formed as z_i * (1 / r_ii) (one reciprocal per column).
+ * Returns MGSA_OK once queued; a numerical failure is reported later by
+ * mgsa_get_info.  If the workspace must grow, this call allocates (and is then
+ * not capturable into a CUDA graph); mgsa_reserve avoids that. */
+mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
+                    mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, mgsa_stream_t s);
+
+/* Wait for stream s and report the outcome of the last mgsa_qr queued on h.
+ * *info = 0 on success; otherwise the 1-based column j at which z_j^T x_j was
+ * not positive (return MGSA_ERR_BREAKDOWN) or not finite (MGSA_ERR_NONFINITE),
+ * or -1 with MGSA_ERR_TIMEOUT.  Columns >= j of Q and R are undefined after a
+ * failure. */
+mgsa_status mgsa_get_info(mgsa_handle h, mgsa_stream_t s, int* info);
+
+/* End-to-end call on HOST buffers (pageable or pinned): copies the CSR arrays
+ * and Z to device buffers owned by the handle, runs mgsa_qr, copies Q and R
+ * back, waits for stream s and returns the outcome as mgsa_get_info would
+ * (with *info set).  Same sizes, layout and requirements as mgsa_qr; the
+ * host arrays must hold rowptr[m+1], col[nnz], val[nnz], Z[ldz*n],
+ * Q[ldq*n], R[ldr*n]. */
+mgsa_status mgsa_qr_host(mgsa_handle h, const int32_t* rowptr, const int32_t* col, const double* val,
+                         int64_t nnz, const double* Z, int64_t m, int n, int64_t ldz, mgsa_variant v,
+                         double* Q, int64_t ldq, double* R, int ldr, mgsa_stream_t s, int* info);
+
+/* Launch parameters of the single-instance kernel (0 restores the default).
+ *   MGSA_PARAM_MAX_CTAS          cap on the number of CTAs (default: one per
+ *                                SM that fits, i.e. the co-resident maximum)
+ *   MGSA_PARAM_CHUNK_ROWS        rows whose pivot vectors are staged in shared
+ *                                memory at once (multiple of 32, <= 4096)
+ *   MGSA_PARAM_MIN_ROWS_PER_CTA  smallest row slab given to one CTA (default 128)
+ * Results stay deterministic for a fixed setting; different settings change the
+ * reduction tree and therefore the last bits of Q and R.  Returns
+ * MGSA_ERR_INVALID for an unknown parameter or an out-of-range value. */
+typedef enum {
+  MGSA_PARAM_MAX_CTAS = 0,
+  MGSA_PARAM_CHUNK_ROWS = 1,
+  MGSA_PARAM_MIN_ROWS_PER_CTA = 2
+} mgsa_param;
+mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value);
+
+/* Short static description of the most recent failure on this thread
+ * (never NULL). */
+const char* mgsa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGSA_H */

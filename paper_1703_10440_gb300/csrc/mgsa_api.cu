@@ -1,0 +1,302 @@
+// C-ABI of libmgsa: handle, argument checks, workspace and launches.
+// The numerical work is done by the kernels in mgsa_sweep.cu.
+#include <algorithm>
+#include <cstring>
+
+#include "mgsa.h"
+#include "mgsa_internal.cuh"
+
+struct mgsa_context {
+  int device = 0;
+  int* ctl = nullptr;          // device control block (status word, barrier state)
+  int* ctl_host = nullptr;     // pinned mirror read by mgsa_get_info
+  double* ws = nullptr;        // X columns + per-CTA partials
+  size_t ws_bytes = 0;
+  unsigned char* io = nullptr; // device staging of mgsa_qr_host
+  size_t io_bytes = 0;
+  int64_t max_ctas = 0;        // MGSA_PARAM_MAX_CTAS (0 = co-resident maximum)
+  int chunk_rows = 0;          // MGSA_PARAM_CHUNK_ROWS (0 = kMaxChunk)
+  int64_t min_rows = 0;        // MGSA_PARAM_MIN_ROWS_PER_CTA (0 = kMinRowsPerCta)
+};
+
+namespace {
+
+thread_local const char* g_last_error = "no error";
+
+mgsa_status fail(mgsa_status s, const char* why) {
+  g_last_error = why;
+  return s;
+}
+
+mgsa_status cuda_fail(cudaError_t e) {
+  g_last_error = cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? MGSA_ERR_NOMEM : MGSA_ERR_CUDA;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = (prev == dev) || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (ok && prev >= 0) {
+      int cur = -1;
+      if (cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+  }
+};
+
+int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+struct Plan {
+  int grid = 1;
+  int64_t rpc = 32;
+  int chunk = 32;
+  size_t smem = 0;
+  int64_t ldx = 0;
+  int xcols = 0;
+  size_t x_bytes = 0;
+  size_t part_bytes = 0;
+};
+
+mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, Plan* p) {
+  const int chunk_cap = h->chunk_rows > 0 ? h->chunk_rows : mgsa::kMaxChunk;
+  const int64_t min_rows = h->min_rows > 0 ? h->min_rows : mgsa::kMinRowsPerCta;
+  int max_ctas = 0;
+  cudaError_t e = mgsa::sweep_max_ctas((int)v, mgsa::sweep_smem_bytes(n, chunk_cap), &max_ctas);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (max_ctas < 1) return fail(MGSA_ERR_CUDA, "sweep kernel does not fit on this device");
+  int64_t g = std::min<int64_t>(max_ctas, (m + min_rows - 1) / min_rows);
+  if (h->max_ctas > 0) g = std::min<int64_t>(g, h->max_ctas);
+  g = std::max<int64_t>(g, 1);
+  p->rpc = round_up((m + g - 1) / g, 32);
+  p->grid = (int)((m + p->rpc - 1) / p->rpc);
+  p->chunk = (int)std::min<int64_t>(chunk_cap, p->rpc);
+  p->smem = mgsa::sweep_smem_bytes(n, p->chunk);
+  p->ldx = round_up(m, 32);
+  p->xcols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
+  p->x_bytes = (size_t)round_up((int64_t)sizeof(double) * p->ldx * p->xcols, 256);
+  p->part_bytes = sizeof(double) * (size_t)(n + 1) * (size_t)p->grid;
+  return MGSA_OK;
+}
+
+mgsa_status ensure_ws(mgsa_handle h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return MGSA_OK;
+  if (h->ws) {
+    cudaError_t e = cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  cudaError_t e = cudaMalloc(&h->ws, bytes);
+  if (e != cudaSuccess) return cuda_fail(e);
+  h->ws_bytes = bytes;
+  return MGSA_OK;
+}
+
+bool ranges_overlap(const void* a, size_t an, const void* b, size_t bn) {
+  const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+  return a0 < b0 + bn && b0 < a0 + an;
+}
+
+mgsa_status check_sizes(int64_t m, int n, int64_t ldz, mgsa_variant v, int64_t ldq, int ldr) {
+  if (n < 1 || n > MGSA_MAX_N) return fail(MGSA_ERR_INVALID, "n must be in [1, MGSA_MAX_N]");
+  if (m < n || m >= ((int64_t)1 << 31)) return fail(MGSA_ERR_INVALID, "m must satisfy n <= m < 2^31");
+  if (ldz < m || ldq < m) return fail(MGSA_ERR_INVALID, "leading dimension of Z or Q below m");
+  if (ldr < n) return fail(MGSA_ERR_INVALID, "leading dimension of R below n");
+  if (v != MGSA_NAIVE && v != MGSA_HA && v != MGSA_HP) return fail(MGSA_ERR_INVALID, "unknown variant");
+  return MGSA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mgsa_last_error(void) { return g_last_error; }
+
+mgsa_status mgsa_create(mgsa_handle* h, int device) {
+  if (!h) return fail(MGSA_ERR_INVALID, "NULL handle pointer");
+  *h = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (device < 0 || device >= count) return fail(MGSA_ERR_INVALID, "no such CUDA device");
+  DeviceGuard g(device);
+  if (!g.ok) return fail(MGSA_ERR_CUDA, "cannot select the device");
+  mgsa_context* c = new (std::nothrow) mgsa_context;
+  if (!c) return fail(MGSA_ERR_NOMEM, "host allocation failed");
+  c->device = device;
+  if ((e = cudaMalloc(&c->ctl, 256)) != cudaSuccess || (e = cudaMemset(c->ctl, 0, 256)) != cudaSuccess ||
+      (e = cudaMallocHost(&c->ctl_host, 256)) != cudaSuccess || (e = mgsa::sweep_prepare(device)) != cudaSuccess) {
+    mgsa_status s = cuda_fail(e);
+    mgsa_destroy(c);
+    return s;
+  }
+  std::memset(c->ctl_host, 0, 256);
+  *h = c;
+  return MGSA_OK;
+}
+
+mgsa_status mgsa_destroy(mgsa_handle h) {
+  if (!h) return MGSA_OK;
+  {
+    DeviceGuard g(h->device);
+    if (h->ws) cudaFree(h->ws);
+    if (h->io) cudaFree(h->io);
+    if (h->ctl) cudaFree(h->ctl);
+    if (h->ctl_host) cudaFreeHost(h->ctl_host);
+  }
+  delete h;
+  return MGSA_OK;
+}
+
+size_t mgsa_workspace_bytes(mgsa_handle h, int64_t m, int n, mgsa_variant v) {
+  if (!h || check_sizes(m, n, m, v, m, n) != MGSA_OK) return 0;
+  DeviceGuard g(h->device);
+  Plan p;
+  if (make_plan(h, m, n, v, &p) != MGSA_OK) return 0;
+  return p.x_bytes + p.part_bytes;
+}
+
+mgsa_status mgsa_reserve(mgsa_handle h, int64_t m, int n, mgsa_variant v) {
+  if (!h) return fail(MGSA_ERR_INVALID, "NULL handle");
+  mgsa_status s = check_sizes(m, n, m, v, m, n);
+  if (s != MGSA_OK) return s;
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(MGSA_ERR_CUDA, "cannot select the device");
+  Plan p;
+  if ((s = make_plan(h, m, n, v, &p)) != MGSA_OK) return s;
+  return ensure_ws(h, p.x_bytes + p.part_bytes);
+}
+
+mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value) {
+  if (!h) return fail(MGSA_ERR_INVALID, "NULL handle");
+  if (value < 0) return fail(MGSA_ERR_INVALID, "parameter value must be >= 0");
+  switch (p) {
+    case MGSA_PARAM_MAX_CTAS: h->max_ctas = value; return MGSA_OK;
+    case MGSA_PARAM_CHUNK_ROWS:
+      if (value % 32 != 0 || value > mgsa::kMaxChunk) return fail(MGSA_ERR_INVALID, "chunk rows: multiple of 32, <= 4096");
+      h->chunk_rows = (int)value;
+      return MGSA_OK;
+    case MGSA_PARAM_MIN_ROWS_PER_CTA: h->min_rows = value; return MGSA_OK;
+    default: return fail(MGSA_ERR_INVALID, "unknown parameter");
+  }
+}
+
+mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
+                    mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, mgsa_stream_t s) {
+  if (!h) return fail(MGSA_ERR_INVALID, "NULL handle");
+  if (!A || !Z || !Q || !R) return fail(MGSA_ERR_INVALID, "NULL matrix pointer");
+  mgsa_status st = check_sizes(m, n, ldz, v, ldq, ldr);
+  if (st != MGSA_OK) return st;
+  if (A->m != m) return fail(MGSA_ERR_INVALID, "A->m differs from m");
+  if (A->nnz < 0 || A->nnz >= ((int64_t)1 << 31)) return fail(MGSA_ERR_INVALID, "nnz must be in [0, 2^31)");
+  if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return fail(MGSA_ERR_INVALID, "NULL CSR array");
+  const size_t zspan = sizeof(double) * (size_t)((n - 1) * ldz + m);
+  const size_t qspan = sizeof(double) * (size_t)((n - 1) * ldq + m);
+  if (ranges_overlap(Z, zspan, Q, qspan)) return fail(MGSA_ERR_INVALID, "Q overlaps Z");
+  const size_t rspan = sizeof(double) * (size_t)((int64_t)(n - 1) * ldr + n);
+  if (ranges_overlap(R, rspan, Q, qspan) || ranges_overlap(R, rspan, Z, zspan))
+    return fail(MGSA_ERR_INVALID, "R overlaps Q or Z");
+
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(MGSA_ERR_CUDA, "cannot select the device");
+  Plan p;
+  if ((st = make_plan(h, m, n, v, &p)) != MGSA_OK) return st;
+  if ((st = ensure_ws(h, p.x_bytes + p.part_bytes)) != MGSA_OK) return st;
+
+  mgsa::SweepArgs a;
+  a.m = m;
+  a.n = n;
+  a.rowptr = A->rowptr;
+  a.col = A->col;
+  a.val = A->val;
+  a.Z = Z;
+  a.ldz = ldz;
+  a.Q = Q;
+  a.ldq = ldq;
+  a.R = R;
+  a.ldr = ldr;
+  a.X = h->ws;
+  a.ldx = p.ldx;
+  a.part = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(h->ws) + p.x_bytes);
+  a.ctl = h->ctl;
+  a.rpc = p.rpc;
+  a.chunk = p.chunk;
+
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+  cudaError_t e = cudaMemsetAsync(h->ctl, 0, sizeof(int) * mgsa::kCtlWords, cs);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = mgsa::sweep_launch((int)v, a, p.grid, p.smem, cs);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return MGSA_OK;
+}
+
+mgsa_status mgsa_get_info(mgsa_handle h, mgsa_stream_t s, int* info) {
+  if (!h || !info) return fail(MGSA_ERR_INVALID, "NULL handle or info");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(MGSA_ERR_CUDA, "cannot select the device");
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+  cudaError_t e = cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(int) * 2, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int code = h->ctl_host[mgsa::kCtlStatus];
+  const int col = h->ctl_host[mgsa::kCtlColumn];
+  switch (code) {
+    case mgsa::kDevOk: *info = 0; return MGSA_OK;
+    case mgsa::kDevBreakdown: *info = col; return fail(MGSA_ERR_BREAKDOWN, "z_j^T A z_j not positive");
+    case mgsa::kDevNonfinite: *info = col; return fail(MGSA_ERR_NONFINITE, "z_j^T A z_j not finite");
+    case mgsa::kDevTimeout: *info = -1; return fail(MGSA_ERR_TIMEOUT, "device-wide wait timed out");
+    default: *info = -1; return fail(MGSA_ERR_CUDA, "unknown device status");
+  }
+}
+
+mgsa_status mgsa_qr_host(mgsa_handle h, const int32_t* rowptr, const int32_t* col, const double* val,
+                         int64_t nnz, const double* Z, int64_t m, int n, int64_t ldz, mgsa_variant v,
+                         double* Q, int64_t ldq, double* R, int ldr, mgsa_stream_t s, int* info) {
+  if (!h || !info) return fail(MGSA_ERR_INVALID, "NULL handle or info");
+  if (!rowptr || !Z || !Q || !R || (nnz > 0 && (!col || !val))) return fail(MGSA_ERR_INVALID, "NULL host pointer");
+  mgsa_status st = check_sizes(m, n, ldz, v, ldq, ldr);
+  if (st != MGSA_OK) return st;
+  if (nnz < 0 || nnz >= ((int64_t)1 << 31)) return fail(MGSA_ERR_INVALID, "nnz must be in [0, 2^31)");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(MGSA_ERR_CUDA, "cannot select the device");
+  // Device staging: rowptr | col | val | Z (ld m) | Q (ld m) | R (ld n), 256-byte aligned pieces.
+  const size_t b_rp = (size_t)round_up(4 * (m + 1), 256), b_col = (size_t)round_up(4 * std::max<int64_t>(nnz, 1), 256);
+  const size_t b_val = (size_t)round_up(8 * std::max<int64_t>(nnz, 1), 256), b_mat = (size_t)round_up(8 * m * n, 256);
+  const size_t b_r = (size_t)round_up(8 * (int64_t)n * n, 256);
+  const size_t need = b_rp + b_col + b_val + 2 * b_mat + b_r;
+  if (need > h->io_bytes) {
+    if (h->io) cudaFree(h->io);
+    h->io = nullptr;
+    h->io_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->io, need);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->io_bytes = need;
+  }
+  unsigned char* base = h->io;
+  int32_t* d_rp = reinterpret_cast<int32_t*>(base);
+  int32_t* d_col = reinterpret_cast<int32_t*>(base + b_rp);
+  double* d_val = reinterpret_cast<double*>(base + b_rp + b_col);
+  double* d_Z = reinterpret_cast<double*>(base + b_rp + b_col + b_val);
+  double* d_Q = reinterpret_cast<double*>(base + b_rp + b_col + b_val + b_mat);
+  double* d_R = reinterpret_cast<double*>(base + b_rp + b_col + b_val + 2 * b_mat);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+  cudaError_t e = cudaMemcpyAsync(d_rp, rowptr, 4 * (m + 1), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col, 4 * nnz, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_val, val, 8 * nnz, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(d_Z, 8 * m, Z, 8 * ldz, 8 * m, n, cudaMemcpyHostToDevice, cs);
+  if (e != cudaSuccess) return cuda_fail(e);
+  mgsa_csr A{m, nnz, d_rp, d_col, d_val};
+  if ((st = mgsa_qr(h, &A, d_Z, m, n, m, v, d_Q, m, d_R, n, s)) != MGSA_OK) return st;
+  e = cudaMemcpy2DAsync(Q, 8 * ldq, d_Q, 8 * m, 8 * m, n, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(R, 8 * (size_t)ldr, d_R, 8 * n, 8 * n, n, cudaMemcpyDeviceToHost, cs);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return mgsa_get_info(h, s, info);
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// Internal declarations shared by the CUDA translation units of libmgsa.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mgsa {
+
+constexpr int kThreads = 512;             // threads per CTA of the single-instance kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxChunk = 4096;           // rows whose pivots are staged in shared memory at once
+constexpr int kMinRowsPerCta = 128;       // smallest row slab worth a CTA
+constexpr unsigned long long kSpinLimitNs = 4000000000ull;  // 4 s bound on any device-wide wait
+
+// Control block layout (int32 words, device memory, zeroed before each launch).
+enum CtlWord { kCtlStatus = 0, kCtlColumn = 1, kCtlBarCount = 2, kCtlBarGen = 3, kCtlWords = 4 };
+
+// Device status codes (equal to the public mgsa_status values).
+enum DevStatus { kDevOk = 0, kDevBreakdown = 2, kDevNonfinite = 3, kDevTimeout = 6 };
+
+enum Variant { kNaive = 0, kHA = 1, kHP = 2 };
+
+struct SweepArgs {
+  int64_t m;
+  int n;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const double* Z;
+  int64_t ldz;
+  double* Q;       // working z_j^{(i)} columns, then q_j
+  int64_t ldq;
+  double* R;
+  int ldr;
+  double* X;       // HP: m x n (x_j, then p_j); HA: x_i in column 0; naive: x_i, p_i in columns 0, 1
+  int64_t ldx;
+  double* part;    // (n + 1) * G partial sums: part[j*G + b] (dots), part[n*G + b] (norm)
+  int* ctl;        // control block (CtlWord)
+  int64_t rpc;     // rows per CTA, multiple of 32
+  int chunk;       // rows per staged chunk, multiple of 32
+};
+
+// Shared memory bytes the single-instance kernel needs for n columns and a chunk.
+inline size_t sweep_smem_bytes(int n, int chunk) {
+  const int kmax = (n + kWarps - 1) / kWarps + 2;
+  return sizeof(double) * (size_t)(3 * chunk + kWarps * kmax + 2 * n + kWarps + 2);
+}
+
+// Launch helpers (defined in mgsa_sweep.cu).
+cudaError_t sweep_prepare(int device);  // sets shared-memory attributes once per device
+cudaError_t sweep_max_ctas(int variant, size_t smem, int* max_ctas);
+cudaError_t sweep_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s);
+
+}  // namespace mgsa

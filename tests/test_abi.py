@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares.
+
+No compute is launched here: these run without a GPU.  Argument checks that
+happen before any CUDA call (NULL handle / pointers) are exercised too.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1703_10440_gb300 import mgsa
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(mgsa_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mgsa_create", "mgsa_qr", "mgsa_get_info", "mgsa_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(mgsa.lib()._name)  # a fresh handle, without the binding's signatures
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert sorted(mgsa.SIGNATURES) == declared_functions()
+
+
+def test_host_side_argument_errors():
+    lib = mgsa.lib()
+    A = mgsa.mgsa_csr(4, 4, None, None, None)
+    st = lib.mgsa_qr(None, ctypes.byref(A), None, 4, 2, 4, 0, None, 4, None, 2, None)
+    assert st == mgsa.MGSA_ERR_INVALID
+    info = ctypes.c_int(0)
+    assert lib.mgsa_get_info(None, None, ctypes.byref(info)) == mgsa.MGSA_ERR_INVALID
+    assert lib.mgsa_create(None, 0) == mgsa.MGSA_ERR_INVALID
+    assert lib.mgsa_destroy(None) == mgsa.MGSA_OK
+    assert isinstance(mgsa.mgsa_last_error(), str)
+
+
+def test_create_without_gpu_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = mgsa.lib().mgsa_create(ctypes.byref(h), 0)
+    assert st in (mgsa.MGSA_ERR_CUDA, mgsa.MGSA_ERR_INVALID)
+    assert h.value is None

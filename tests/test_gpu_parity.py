@@ -1,0 +1,215 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Gates (floating point, from the paper's error analysis, Section 3):
+  representation  ||Z - QR||_F / ||Z||_F  <= max(1e-13, 10 x oracle's value)
+  A-orthogonality ||I - Q^T A Q||_F       <= max(1e-12, 10 x oracle's value)
+  R               ||R - R_oracle||_F / ||R||_F <= 1e-10  when kappa(Z) <= 1e3
+  element-wise    |Q - Q_oracle| <= 1e-9 * kappa(R) * max|Q_oracle|, likewise R
+Both sides run the same algorithm (naive/HA/HP, right-looking); they differ only
+in rounding (fused multiply-add, reduction tree, reciprocal scaling).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1703_10440_gb300 import mgsa  # noqa: E402
+
+VARIANTS = ["naive", "ha", "hp"]
+
+
+@pytest.fixture(scope="module")
+def handle():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    h = mgsa.Handle(0)
+    yield h
+    h.close()
+
+
+def to_dev(A, Z):
+    d = torch.device("cuda")
+    rowptr, col, val = A
+    Ad = (torch.from_numpy(np.ascontiguousarray(rowptr)).to(d), torch.from_numpy(np.ascontiguousarray(col)).to(d),
+          torch.from_numpy(np.ascontiguousarray(val)).to(d))
+    Zd = torch.from_numpy(np.ascontiguousarray(np.asarray(Z).T)).to(d).T
+    return Ad, Zd
+
+
+def gpu_qr(h, A, Z, variant):
+    Ad, Zd = to_dev(A, Z)
+    Q, R = h.qr(Ad, Zd, variant)
+    st, info = h.info()
+    return Q.cpu().numpy(), R.cpu().numpy(), st, info
+
+
+def check_parity(A, Z, variant, Q, R, well_conditioned=True):
+    Qo, Ro, info, _, _ = oracle.mgs(A, Z, variant, "row")
+    assert info == 0
+    rep_o, rep_g = oracle.repr_error(Z, Qo, Ro), oracle.repr_error(Z, Q, R)
+    loss_o, loss_g = oracle.orth_loss(A, Qo), oracle.orth_loss(A, Q)
+    assert rep_g <= max(1e-13, 10 * rep_o), (rep_g, rep_o)
+    assert loss_g <= max(1e-12, 10 * loss_o), (loss_g, loss_o)
+    assert np.all(np.tril(R, -1) == 0.0) and np.all(np.diag(R) > 0)
+    if well_conditioned:
+        assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 1e-10
+        kR = np.linalg.cond(Ro)
+        assert np.abs(R - Ro).max() <= 1e-9 * kR * np.abs(Ro).max()
+        assert np.abs(Q - Qo).max() <= 1e-9 * kR * np.abs(Qo).max()
+    return rep_g, loss_g
+
+
+SMALL_CASES = {
+    "tridiag_1x1": lambda: W.tridiag(1, 1),
+    "tridiag_2x2": lambda: W.tridiag(2, 2),
+    "tridiag_3x1": lambda: W.tridiag(3, 1),
+    "tridiag_17x3": lambda: W.tridiag(17, 3),
+    "tridiag_100x16": lambda: W.tridiag(100, 16),
+    "tridiag_257x33": lambda: W.tridiag(257, 33),
+    "tridiag_4096x16": lambda: W.tridiag(4096, 16),
+    "tridiag_5003x7": lambda: W.tridiag(5003, 7),
+    "banded_777x20": lambda: W.banded(777, 20, seed=3),
+    "banded_3000x64": lambda: W.banded(3000, 64, seed=4),
+    "banded_20011x40": lambda: W.banded(20011, 40, seed=5),
+    "varcoef3d_12": lambda: W.varcoef3d(side=12, n=24),
+}
+
+
+@pytest.mark.parametrize("case", sorted(SMALL_CASES))
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_small(handle, case, variant):
+    A, Z = SMALL_CASES[case]()
+    Q, R, st, info = gpu_qr(handle, A, Z, variant)
+    assert (st, info) == (mgsa.MGSA_OK, 0)
+    check_parity(A, Z, variant, Q, R)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_graded_poisson(handle, variant):
+    # kappa(Z) = 1e6: HA/HP accuracy stress at a size the oracle finishes quickly.
+    A, Z = W.poisson2d(side=48, n=32)
+    Q, R, st, info = gpu_qr(handle, A, Z, variant)
+    assert (st, info) == (mgsa.MGSA_OK, 0)
+    check_parity(A, Z, variant, Q, R, well_conditioned=False)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_dense_exp2(handle, variant):
+    # Section 4.2 family, case 2 (worst case), moderate conditioning.
+    Ad, Z, _ = W.exp2_problem(4.0, 2.0, case=2)
+    A = W.dense_csr(Ad)
+    Q, R, st, info = gpu_qr(handle, A, Z, variant)
+    assert (st, info) == (mgsa.MGSA_OK, 0)
+    check_parity(A, Z, variant, Q, R)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("max_ctas,chunk", [(1, 32), (3, 256), (7, 4096), (2, 96)])
+def test_parity_forced_tiling(handle, variant, max_ctas, chunk):
+    """Few CTAs and small chunks: many chunks per CTA, ragged last chunk."""
+    A, Z = W.banded(5003, 12, seed=6)
+    handle.set_param(mgsa.MGSA_PARAM_MAX_CTAS, max_ctas)
+    handle.set_param(mgsa.MGSA_PARAM_CHUNK_ROWS, chunk)
+    try:
+        Q, R, st, info = gpu_qr(handle, A, Z, variant)
+    finally:
+        handle.set_param(mgsa.MGSA_PARAM_MAX_CTAS, 0)
+        handle.set_param(mgsa.MGSA_PARAM_CHUNK_ROWS, 0)
+    assert (st, info) == (mgsa.MGSA_OK, 0)
+    check_parity(A, Z, variant, Q, R)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_deterministic(handle, variant):
+    A, Z = W.banded(40000, 24, seed=7)
+    Q1, R1, st1, _ = gpu_qr(handle, A, Z, variant)
+    Q2, R2, st2, _ = gpu_qr(handle, A, Z, variant)
+    assert st1 == st2 == mgsa.MGSA_OK
+    assert np.array_equal(Q1, Q2) and np.array_equal(R1, R2)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_breakdown_and_recovery(handle, variant):
+    m, n = 300, 5
+    rowptr = np.arange(m + 1, dtype=np.int32)
+    col = np.arange(m, dtype=np.int32)
+    val = np.ones(m)
+    val[0] = -1.0
+    Z = np.asfortranarray(np.eye(m, n))
+    _, _, st, info = gpu_qr(handle, (rowptr, col, val), Z, variant)
+    assert (st, info) == (mgsa.MGSA_ERR_BREAKDOWN, 1)
+    Z = np.asfortranarray(W.rng(3, 200).standard_normal((m, n)))
+    Z[:, 2] = 0.0
+    _, _, st, info = gpu_qr(handle, W.tridiag_csr(m), Z, variant)
+    assert (st, info) == (mgsa.MGSA_ERR_BREAKDOWN, 3)
+    Z[:, 2] = 1.0
+    Z[7, 1] = np.nan
+    _, _, st, info = gpu_qr(handle, W.tridiag_csr(m), Z, variant)
+    assert (st, info) == (mgsa.MGSA_ERR_NONFINITE, 2)
+    # the handle keeps working after a failure
+    A, Z = W.tridiag(m, n)
+    Q, R, st, info = gpu_qr(handle, A, Z, variant)
+    assert (st, info) == (mgsa.MGSA_OK, 0)
+    check_parity(A, Z, variant, Q, R)
+
+
+def test_invalid_arguments_rejected_before_launch(handle):
+    A, Z = W.tridiag(64, 8)
+    Ad, Zd = to_dev(A, Z)
+    csr = mgsa.make_csr(64, len(A[1]), *Ad)
+    Q = torch.empty((8, 64), dtype=torch.float64, device="cuda").T
+    R = torch.empty((8, 8), dtype=torch.float64, device="cuda").T
+    bad = [
+        dict(m=64, n=0, ldz=64, ldq=64, ldr=8),
+        dict(m=4, n=8, ldz=64, ldq=64, ldr=8),
+        dict(m=64, n=8, ldz=63, ldq=64, ldr=8),
+        dict(m=64, n=8, ldz=64, ldq=64, ldr=7),
+        dict(m=64, n=mgsa.MGSA_MAX_N + 1, ldz=64, ldq=64, ldr=8),
+    ]
+    for b in bad:
+        st = mgsa.mgsa_qr(handle.h, csr, Zd, b["m"], b["n"], b["ldz"], mgsa.MGSA_HP, Q, b["ldq"], R, b["ldr"])
+        assert st == mgsa.MGSA_ERR_INVALID, b
+    # Q overlapping Z
+    st = mgsa.mgsa_qr(handle.h, csr, Zd, 64, 8, 64, mgsa.MGSA_HP, Zd, 64, R, 8)
+    assert st == mgsa.MGSA_ERR_INVALID
+    # A->m mismatch
+    csr_bad = mgsa.make_csr(65, len(A[1]), *Ad)
+    st = mgsa.mgsa_qr(handle.h, csr_bad, Zd, 64, 8, 64, mgsa.MGSA_HP, Q, 64, R, 8)
+    assert st == mgsa.MGSA_ERR_INVALID
+    assert mgsa.mgsa_qr(handle.h, csr, Zd, 64, 8, 64, 7, Q, 64, R, 8) == mgsa.MGSA_ERR_INVALID
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_leading_dimensions(handle, variant):
+    """Z, Q, R inside larger column-major buffers (ld > m, ld > n)."""
+    A, Z = W.banded(1000, 9, seed=8)
+    Ad, _ = to_dev(A, Z)
+    d = torch.device("cuda")
+    Zbig = torch.full((9, 1037), 7.0, dtype=torch.float64, device=d)
+    Zbig[:, :1000] = torch.from_numpy(np.ascontiguousarray(Z.T)).to(d)
+    Qbig = torch.full((9, 1100), -3.0, dtype=torch.float64, device=d)
+    Rbig = torch.full((9, 11), -5.0, dtype=torch.float64, device=d)
+    csr = mgsa.make_csr(1000, len(A[1]), *Ad)
+    st = mgsa.mgsa_qr(handle.h, csr, Zbig, 1000, 9, 1037, mgsa.VARIANTS[variant], Qbig, 1100, Rbig, 11)
+    assert st == mgsa.MGSA_OK
+    assert handle.info() == (mgsa.MGSA_OK, 0)
+    Qb, Rb = Qbig.cpu().numpy(), Rbig.cpu().numpy()
+    assert np.all(Qb[:, 1000:] == -3.0) and np.all(Rb[:, 9:] == -5.0)
+    check_parity(A, Z, variant, np.asfortranarray(Qb[:, :1000].T), np.asfortranarray(Rb[:, :9].T))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_host_entry_point_matches_device(handle, variant):
+    A, Z = W.banded(2500, 13, seed=9)
+    Qd, Rd, st, _ = gpu_qr(handle, A, Z, variant)
+    Qh = np.zeros((2500, 13), order="F")
+    Rh = np.zeros((13, 13), order="F")
+    rowptr, col, val = A
+    st, info = mgsa.mgsa_qr_host(handle.h, rowptr, col, val, len(col), np.asfortranarray(Z), 2500, 13, 2500,
+                                 mgsa.VARIANTS[variant], Qh, 2500, Rh, 13)
+    assert (st, info) == (mgsa.MGSA_OK, 0)
+    assert np.array_equal(Qh, Qd) and np.array_equal(Rh, Rd)

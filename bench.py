@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark: A-orthonormal MGS thin QRs per second on GB300.
+
+One step is one pass of the whole hot path over one synthetic input: the
+same Z is factored by the three forms of the method -- naive (2n MV), MGS-HA
+(n MV) and MGS-HP (one block product) -- so a step is 3 QRs and covers the
+block SpMM, the per-column SpMVs, the diagonal, the A-dot rows and both
+rank-1 updates.  Each QR is one cooperative kernel launch of libmgsa.
+
+Default workload: 2D 5-point Laplacian on a 512 x 512 grid + 0.01 I
+(m = 262144, CSR FP64) and Z = G diag(logspace(0, -6, 64)), G ~ N(0,1)
+(kappa(Z) ~ 1e6).  L2 is flushed (a 256 MiB write) before every timed QR and
+each QR is timed with CUDA events on its own stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mgsa|reference]
+                    [--workload poisson2d|varcoef3d|tridiag]
+
+``--impl reference`` times the CPU oracle (plain C, one core) on the same
+workload: each step is one QR, the variants taking turns.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "A-MGS QRs/sec & % HBM roofline (n-MV vs 2n-MV); served p50/p99 latency"
+UNIT = "QR/s"
+VARIANTS = ("naive", "ha", "hp")
+L2_FLUSH_BYTES = 256 << 20
+# Peaks: measured HBM copy bandwidth (generated file) and the FP64 FMA
+# peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop
+# x 2.07 GHz = 1.259 TFLOP/s (the recipe's nominal 1.25 TFLOP/s FP64).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1703_10440_gb300/csrc/mgsa_sweep.cu", "paper_1703_10440_gb300/csrc/mgsa_internal.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+
+
+# ---------------------------------------------------------------------------
+# Workloads and the algorithmic byte / flop models of each form
+# ---------------------------------------------------------------------------
+
+def make_workload(name: str):
+    if name == "poisson2d":
+        A, Z = W.poisson2d()
+        desc = "poisson2d_512x512_shift0.01_n64_kappaZ1e6"
+    elif name == "varcoef3d":
+        A, Z = W.varcoef3d()
+        desc = "varcoef3d_128cubed_shift1e-3_n128"
+    elif name == "tridiag":
+        A, Z = W.tridiag()
+        desc = "tridiag_m4096_n16"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return desc, A, Z
+
+
+def model(variant: str, m: int, n: int, nnz: int) -> tuple[float, float]:
+    """Algorithmic (bytes, flops) of one QR in the right-looking one-pass-per-step form.
+
+    c = 8m bytes per column, B_A = 12 nnz + 4(m+1) bytes of CSR.
+    bytes  naive: 2n(B_A + 2c) + c n(n-1) + 2cn   (2n MV; z_j read+written per pair)
+           HA:     n(B_A + 2c) + c n(n-1) + 2cn   (n MV)
+           HP:     B_A + 2cn + 2c n(n-1) + 2cn    (one block product; z_j and x_j per pair)
+    flops  per pair (i<j): dot + z-update (2 flop each per row), HP also x-update;
+           per column: z^T x (2m), scaling by 1/r_ii (m per vector); MV 2 nnz.
+    """
+    c = 8.0 * m
+    BA = 12.0 * nnz + 4.0 * (m + 1)
+    pairs = n * (n - 1) / 2.0
+    if variant == "naive":
+        return 2 * n * (BA + 2 * c) + c * n * (n - 1) + 2 * c * n, 4.0 * m * pairs + 2.0 * m * n + m * n + 4.0 * nnz * n
+    if variant == "ha":
+        return n * (BA + 2 * c) + c * n * (n - 1) + 2 * c * n, 4.0 * m * pairs + 2.0 * m * n + 2.0 * m * n + 2.0 * nnz * n
+    return BA + 2 * c * n + 2 * c * n * (n - 1) + 2 * c * n, 6.0 * m * pairs + 2.0 * m * n + 2.0 * m * n + 2.0 * nnz * n
+
+
+def hbm_peak() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(workload: str, variant: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source."""
+    try:
+        rows = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 4 and not line.startswith("#"):
+                    rows[(parts[0], parts[1])] = (parts[2], float(parts[3]))
+        src, val = rows[(workload, variant)]
+        return val if src == kernel_source_hash() else None
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self) -> dict:
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def time_oracle(A, Z, variants) -> float:
+    import oracle
+
+    oracle.load()
+    t0 = time.perf_counter()
+    for v in variants:
+        _, _, info, _, _ = oracle.mgs(A, Z, v, "row")
+        if info != 0:
+            raise RuntimeError(f"oracle breakdown in {v}")
+    return time.perf_counter() - t0
+
+
+def run_reference(args, desc, A, Z, rank):
+    if rank != 0:
+        return
+    m, n = Z.shape
+    for k in range(args.warmup):
+        time_oracle(A, Z, [VARIANTS[k % 3]])
+    secs = [time_oracle(A, Z, [VARIANTS[k % 3]]) for k in range(args.steps)]
+    total = sum(secs)
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "m": m, "n": n, "nnz": int(len(A[1])),
+                       "step": "one QR, the variants naive/ha/hp taking turns"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} single-threaded oracle QRs (plain C FP64, row form) of the "
+                                       f"{desc} workload, variants rotating"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, desc, A, Z, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1703_10440_gb300 import mgsa
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    m, n = Z.shape
+    nnz = int(len(A[1]))
+    rowptr, col, val = A
+    Ad = tuple(torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (rowptr, col, val))
+    Zd = torch.from_numpy(np.ascontiguousarray(Z.T)).to(dev).T
+    Q = torch.empty((n, m), dtype=torch.float64, device=dev).T
+    R = torch.empty((n, n), dtype=torch.float64, device=dev).T
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = mgsa.Handle(local_rank)
+    for v in VARIANTS:
+        mgsa.mgsa_reserve(h.h, m, n, mgsa.VARIANTS[v])
+
+    def one_qr(v):
+        h.qr_into(Ad, Zd, Q, R, v, stream)
+
+    for _ in range(args.warmup):
+        for v in VARIANTS:
+            flush.fill_(1)
+            one_qr(v)
+    st = h.info(stream)
+    if st != (mgsa.MGSA_OK, 0):
+        raise RuntimeError(f"warm-up QR failed: {st}")
+
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in VARIANTS]
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            for vi, v in enumerate(VARIANTS):
+                flush.fill_(k & 0xFF)
+                ev[k][vi][0].record(stream)
+                one_qr(v)
+                ev[k][vi][1].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    st = h.info(stream)
+    if st != (mgsa.MGSA_OK, 0):
+        raise RuntimeError(f"timed QR failed: {st}")
+    per_variant_ms = [sum(ev[k][vi][0].elapsed_time(ev[k][vi][1]) for k in range(args.steps)) / args.steps
+                      for vi in range(len(VARIANTS))]
+    step_ms = sum(per_variant_ms)
+    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms_max = float(t.item())
+
+    # End to end through the host-buffer entry point: copies in, QR, copies out.
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        h_rp, h_col, h_val, h_Z = pin(rowptr), pin(col), pin(val), pin(np.asfortranarray(Z).T)
+        h_Q = torch.empty((n, m), dtype=torch.float64).pin_memory()
+        h_R = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        ksteps = max(3, min(args.steps, 10))
+
+        def e2e_step():
+            for v in VARIANTS:
+                r = mgsa.mgsa_qr_host(h.h, h_rp, h_col, h_val, nnz, h_Z, m, n, m, mgsa.VARIANTS[v], h_Q, m, h_R, n,
+                                      stream)
+                if r != (mgsa.MGSA_OK, 0):
+                    raise RuntimeError(f"mgsa_qr_host failed: {r}")
+        e2e_step()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        e2e_ms = 1e3 * (time.perf_counter() - t0) / ksteps
+        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_ms = float(te.item())
+        h2d = 3 * (rowptr.nbytes + col.nbytes + val.nbytes + Z.nbytes)
+        d2h = 3 * (8 * m * n + 8 * n * n)
+        e2e = {"value": world * 3 * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": ksteps}
+    h.close()
+
+    if rank != 0:
+        return
+    peak_hbm, peak_src = hbm_peak()
+    per_variant = {}
+    for vi, v in enumerate(VARIANTS):
+        b, fl = model(v, m, n, nnz)
+        ms = per_variant_ms[vi]
+        gbs = b / ms / 1e6
+        tfl = fl / ms / 1e9
+        per_variant[v] = {"ms": round(ms, 4), "qr_per_s": round(1e3 / ms, 2), "model_bytes": b, "model_flops": fl,
+                          "model_GBs": round(gbs, 1), "hbm_frac": round(gbs / peak_hbm, 4),
+                          "fp64_tflops": round(tfl, 4), "fp64_frac": round(tfl / FP64_PEAK_TFLOPS, 4)}
+    # Dominant kernel: the longest of the three launches of a step.
+    dom = max(VARIANTS, key=lambda v: per_variant[v]["ms"])
+    pv = per_variant[dom]
+    if pv["fp64_frac"] >= pv["hbm_frac"]:
+        roof = {"bound": "alu", "achieved": pv["fp64_tflops"], "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": pv["fp64_frac"]}
+    else:
+        roof = {"bound": "hbm", "achieved": pv["model_GBs"], "peak": peak_hbm, "unit": "GB/s", "frac": pv["hbm_frac"]}
+    traffic = read_traffic(desc, dom)
+    roof.update({"traffic": traffic, "kernel": f"mgs_sweep_kernel<{dom}>",
+                 "algorithmic_bytes": pv["model_bytes"], "algorithmic_flops": pv["model_flops"],
+                 "hbm_frac_of_" + peak_src: pv["hbm_frac"], "fp64_frac_of_derived_peak": pv["fp64_frac"]})
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        secs = time_oracle(A, Z, VARIANTS)
+        cpu = {"value": 3.0 / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one single-threaded oracle QR per variant (naive, ha, hp; plain C FP64, row form) of the "
+                         f"same {desc} input: {secs:.2f} s"}
+
+    value = world * 3 * 1e3 / step_ms_max
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "m": m, "n": n, "nnz": nnz, "step": "3 QRs: naive, ha, hp on the same Z",
+                       "l2": "flushed (256 MiB write) before every timed QR", "parallelism": f"replicas{world}"},
+            "per_variant": per_variant, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mgsa", choices=["mgsa", "reference"])
+    ap.add_argument("--workload", default="poisson2d", choices=["poisson2d", "varcoef3d", "tridiag"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            desc, A, Z = make_workload(args.workload)
+            run_reference(args, desc, A, Z, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    desc, A, Z = make_workload(args.workload)
+    run_gpu(args, desc, A, Z, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

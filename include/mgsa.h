@@ -154,6 +154,40 @@ typedef enum {
 } mgsa_param;
 mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value);
 
+/* Allocation-free QR.  The paper has no counterpart to this entry point; it
+ * exists for callers that must not allocate device memory themselves: code
+ * running under a memory manager that owns the whole device (a framework's
+ * caching allocator, a server that admits work against a fixed memory
+ * budget) and may not allocate behind its back, and latency-critical loops
+ * where cudaMalloc / cudaFree would add device-wide synchronisation.  It
+ * computes what mgsa_qr computes, with the same kernel, but needs no handle
+ * and allocates nothing: its scratch (the x / p columns, the per-CTA
+ * partial sums and the status / barrier words) lives in one static device
+ * array of MGSA_NOALLOC_SCRATCH_BYTES bytes compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ *   A, Z, Q, R, m, n, ldz, ldq, ldr, v   as for mgsa_qr.
+ *   info_dev  NULL, or device memory for two int32 written after the QR:
+ *             info_dev[0] = 0 (success), 2 (z_j^T x_j <= 0), 3 (not finite)
+ *             or 6 (a device-wide wait timed out); info_dev[1] = the 1-based
+ *             column j of the failure (-1 for a timeout).
+ *   s         stream; the call returns without waiting.
+ *
+ * Runs on the current CUDA device; every pointer must be on that device.
+ * The first call on a device sets that device up (looks up the address of
+ * the static array and sets the kernel's shared-memory limit); make that
+ * first call before any stream capture.  Problems whose scratch does not fit
+ * (about 8*(m*c + 2049*G) bytes with c = n for HP, 1 for HA, 2 for naive and
+ * G <= the number of SMs) are rejected with MGSA_ERR_INVALID and a message
+ * in mgsa_last_error; nothing is launched then.  Every call uses the same
+ * array and leaves its contents behind (the status and barrier words are
+ * cleared at the start of each call), so calls whose work overlaps on the
+ * GPU -- on different streams, or from different threads -- race and give
+ * undefined results; order them on one stream. */
+#define MGSA_NOALLOC_SCRATCH_BYTES (32u << 20)
+mgsa_status mgsa_qr_noalloc(const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz, mgsa_variant v,
+                            double* Q, int64_t ldq, double* R, int ldr, int* info_dev, mgsa_stream_t s);
+
 /* Short static description of the most recent failure on this thread
  * (never NULL). */
 const char* mgsa_last_error(void);

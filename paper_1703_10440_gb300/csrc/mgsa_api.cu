@@ -113,6 +113,9 @@ mgsa_status check_sizes(int64_t m, int n, int64_t ldz, mgsa_variant v, int64_t l
 
 }  // namespace
 
+// Lets other translation units of the library report through mgsa_last_error.
+void mgsa::set_last_error(const char* why) { g_last_error = why; }
+
 extern "C" {
 
 const char* mgsa_last_error(void) { return g_last_error; }

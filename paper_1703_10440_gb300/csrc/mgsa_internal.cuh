@@ -46,6 +46,9 @@ inline size_t sweep_smem_bytes(int n, int chunk) {
   return sizeof(double) * (size_t)(3 * chunk + kWarps * kmax + 2 * n + kWarps + 2);
 }
 
+// Records the message mgsa_last_error returns on this thread (mgsa_api.cu).
+void set_last_error(const char* why);
+
 // Launch helpers (defined in mgsa_sweep.cu).
 cudaError_t sweep_prepare(int device);  // sets shared-memory attributes once per device
 cudaError_t sweep_max_ctas(int variant, size_t smem, int* max_ctas);

@@ -1,0 +1,141 @@
+// mgsa_qr_noalloc: the single-instance QR with its scratch in a static device
+// array instead of handle-owned allocations (declared in mgsa.h).
+//
+// Who needs it: callers that may not allocate device memory -- code living
+// under a memory manager that owns the whole GPU (a caching allocator, a
+// server admitting work against a fixed budget) and latency-critical loops
+// that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+//
+// The kernel is the same cooperative kernel mgsa_qr launches; only the
+// source of its scratch differs.  The array below is module data: every GPU
+// that loads the library holds it until the process exits.  Host code may not
+// use its name as a device address (on the host it names a stand-in), so the
+// first call on each device, with that device current, looks the address up
+// with cudaGetSymbolAddress and remembers it.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "mgsa.h"
+#include "mgsa_internal.cuh"
+
+namespace {
+
+constexpr size_t kScratchBytes = MGSA_NOALLOC_SCRATCH_BYTES;
+constexpr size_t kCtlBytes = 256;  // status + barrier words, then padding
+constexpr int kMaxDevices = 64;
+
+// Layout of one call's scratch: [ctl: 256 B][per-CTA partials][x / p columns].
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_setup_mutex;
+void* g_scratch_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+mgsa_status fail(mgsa_status s, const char* why) {
+  mgsa::set_last_error(why);
+  return s;
+}
+
+mgsa_status cuda_fail(cudaError_t e) {
+  mgsa::set_last_error(cudaGetErrorString(e));
+  return MGSA_ERR_CUDA;
+}
+
+// Once per device, with that device current: the array's device address and
+// the kernel's shared-memory attribute.
+mgsa_status device_setup(int dev, unsigned char** scratch) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(MGSA_ERR_INVALID, "device ordinal beyond the set-up table");
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if ((e = mgsa::sweep_prepare(dev)) != cudaSuccess) return cuda_fail(e);
+    g_scratch_addr[dev] = p;
+  }
+  *scratch = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  return MGSA_OK;
+}
+
+bool overlap(const void* a, size_t an, const void* b, size_t bn) {
+  const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+  return a0 < b0 + bn && b0 < a0 + an;
+}
+
+}  // namespace
+
+extern "C" mgsa_status mgsa_qr_noalloc(const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
+                                       mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, int* info_dev,
+                                       mgsa_stream_t s) {
+  if (!A || !Z || !Q || !R) return fail(MGSA_ERR_INVALID, "NULL matrix pointer");
+  if (n < 1 || n > MGSA_MAX_N) return fail(MGSA_ERR_INVALID, "n must be in [1, MGSA_MAX_N]");
+  if (m < n || m >= ((int64_t)1 << 31)) return fail(MGSA_ERR_INVALID, "m must satisfy n <= m < 2^31");
+  if (ldz < m || ldq < m || ldr < n) return fail(MGSA_ERR_INVALID, "leading dimension too small");
+  if (v != MGSA_NAIVE && v != MGSA_HA && v != MGSA_HP) return fail(MGSA_ERR_INVALID, "unknown variant");
+  if (A->m != m) return fail(MGSA_ERR_INVALID, "A->m differs from m");
+  if (A->nnz < 0 || A->nnz >= ((int64_t)1 << 31)) return fail(MGSA_ERR_INVALID, "nnz must be in [0, 2^31)");
+  if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return fail(MGSA_ERR_INVALID, "NULL CSR array");
+  const size_t zspan = sizeof(double) * (size_t)((n - 1) * ldz + m);
+  const size_t qspan = sizeof(double) * (size_t)((n - 1) * ldq + m);
+  const size_t rspan = sizeof(double) * (size_t)((int64_t)(n - 1) * ldr + n);
+  if (overlap(Z, zspan, Q, qspan) || overlap(R, rspan, Q, qspan) || overlap(R, rspan, Z, zspan))
+    return fail(MGSA_ERR_INVALID, "Q, R and Z must not overlap");
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  unsigned char* scratch = nullptr;
+  mgsa_status st = device_setup(dev, &scratch);
+  if (st != MGSA_OK) return st;
+
+  // Launch shape: the defaults of mgsa_qr (one CTA per SM that fits, slabs of
+  // at least kMinRowsPerCta rows, pivot chunks of kMaxChunk rows).
+  int max_ctas = 0;
+  if ((e = mgsa::sweep_max_ctas((int)v, mgsa::sweep_smem_bytes(n, mgsa::kMaxChunk), &max_ctas)) != cudaSuccess)
+    return cuda_fail(e);
+  if (max_ctas < 1) return fail(MGSA_ERR_CUDA, "sweep kernel does not fit on this device");
+  int64_t g = std::min<int64_t>(max_ctas, (m + mgsa::kMinRowsPerCta - 1) / mgsa::kMinRowsPerCta);
+  g = std::max<int64_t>(g, 1);
+  const int64_t rpc = round_up((m + g - 1) / g, 32);
+  const int grid = (int)((m + rpc - 1) / rpc);
+  const int chunk = (int)std::min<int64_t>(mgsa::kMaxChunk, rpc);
+  const size_t smem = mgsa::sweep_smem_bytes(n, chunk);
+  const int64_t ldx = round_up(m, 32);
+  const int xcols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
+  const size_t part_bytes = (size_t)round_up((int64_t)sizeof(double) * (n + 1) * grid, 256);
+  const size_t x_bytes = sizeof(double) * (size_t)ldx * (size_t)xcols;
+  if (kCtlBytes + part_bytes + x_bytes > kScratchBytes)
+    return fail(MGSA_ERR_INVALID,
+                "problem too large for mgsa_qr_noalloc: its scratch exceeds MGSA_NOALLOC_SCRATCH_BYTES (32 MiB); "
+                "use mgsa_qr");
+
+  mgsa::SweepArgs a;
+  a.m = m;
+  a.n = n;
+  a.rowptr = A->rowptr;
+  a.col = A->col;
+  a.val = A->val;
+  a.Z = Z;
+  a.ldz = ldz;
+  a.Q = Q;
+  a.ldq = ldq;
+  a.R = R;
+  a.ldr = ldr;
+  a.ctl = reinterpret_cast<int*>(scratch);
+  a.part = reinterpret_cast<double*>(scratch + kCtlBytes);
+  a.X = reinterpret_cast<double*>(scratch + kCtlBytes + part_bytes);
+  a.ldx = ldx;
+  a.rpc = rpc;
+  a.chunk = chunk;
+
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+  // The status and barrier words must start at zero; the rest of the array is
+  // written before it is read.
+  if ((e = cudaMemsetAsync(a.ctl, 0, sizeof(int) * mgsa::kCtlWords, cs)) != cudaSuccess) return cuda_fail(e);
+  if ((e = mgsa::sweep_launch((int)v, a, grid, smem, cs)) != cudaSuccess) return cuda_fail(e);
+  if (info_dev && (e = cudaMemcpyAsync(info_dev, a.ctl, 2 * sizeof(int), cudaMemcpyDeviceToDevice, cs)) != cudaSuccess)
+    return cuda_fail(e);
+  return MGSA_OK;
+}

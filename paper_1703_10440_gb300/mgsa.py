@@ -29,6 +29,7 @@ MGSA_ERR_TIMEOUT = 6
 STATUS_NAMES = {0: "MGSA_OK", 1: "MGSA_ERR_INVALID", 2: "MGSA_ERR_BREAKDOWN", 3: "MGSA_ERR_NONFINITE",
                 4: "MGSA_ERR_NOMEM", 5: "MGSA_ERR_CUDA", 6: "MGSA_ERR_TIMEOUT"}
 MGSA_MAX_N = 2048
+MGSA_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class mgsa_csr(ctypes.Structure):
@@ -57,6 +58,7 @@ SIGNATURES = {
     "mgsa_qr_host": (_INT, [_VP, _VP, _VP, _VP, _I64, _VP, _I64, _INT, _I64, _INT, _VP, _I64, _VP, _INT, _VP,
                             ctypes.POINTER(_INT)]),
     "mgsa_set_param": (_INT, [_VP, _INT, _I64]),
+    "mgsa_qr_noalloc": (_INT, [ctypes.POINTER(mgsa_csr), _VP, _I64, _INT, _I64, _INT, _VP, _I64, _VP, _INT, _VP, _VP]),
     "mgsa_last_error": (ctypes.c_char_p, []),
 }
 MGSA_PARAM_MAX_CTAS, MGSA_PARAM_CHUNK_ROWS, MGSA_PARAM_MIN_ROWS_PER_CTA = 0, 1, 2
@@ -141,6 +143,14 @@ def mgsa_qr(h: int, A: mgsa_csr, Z, m: int, n: int, ldz: int, variant: int, Q, l
     """Queue one QR; returns the status (MGSA_OK or an argument error)."""
     return int(lib().mgsa_qr(h, ctypes.byref(A), _ptr(Z), m, n, ldz, variant, _ptr(Q), ldq, _ptr(R), ldr,
                              _stream(stream)))
+
+
+def mgsa_qr_noalloc(A: mgsa_csr, Z, m: int, n: int, ldz: int, variant: int, Q, ldq: int, R, ldr: int, info_dev=None,
+                    stream=None) -> int:
+    """Queue one QR whose scratch is the library's static device array (no
+    allocation, no handle); returns the status of the call."""
+    return int(lib().mgsa_qr_noalloc(ctypes.byref(A), _ptr(Z), m, n, ldz, variant, _ptr(Q), ldq, _ptr(R), ldr,
+                                     _ptr(info_dev), _stream(stream)))
 
 
 def mgsa_get_info(h: int, stream=None) -> tuple[int, int]:

@@ -177,7 +177,7 @@ mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value);
  * The first call on a device sets that device up (looks up the address of
  * the static array and sets the kernel's shared-memory limit); make that
  * first call before any stream capture.  Problems whose scratch does not fit
- * (about 8*(m*c + 2049*G) bytes with c = n for HP, 1 for HA, 2 for naive and
+ * (about 8*(m*c + (2n+1)*G) bytes with c = n for HP, 1 for HA, 2 for naive and
  * G <= the number of SMs) are rejected with MGSA_ERR_INVALID and a message
  * in mgsa_last_error; nothing is launched then.  Every call uses the same
  * array and leaves its contents behind (the status and barrier words are

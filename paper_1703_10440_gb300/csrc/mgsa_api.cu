@@ -79,7 +79,7 @@ mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, P
   p->ldx = round_up(m, 32);
   p->xcols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
   p->x_bytes = (size_t)round_up((int64_t)sizeof(double) * p->ldx * p->xcols, 256);
-  p->part_bytes = sizeof(double) * (size_t)(n + 1) * (size_t)p->grid;
+  p->part_bytes = sizeof(double) * (size_t)(2 * n + 1) * (size_t)p->grid;
   return MGSA_OK;
 }
 

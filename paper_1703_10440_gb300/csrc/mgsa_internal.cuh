@@ -13,6 +13,7 @@ constexpr int kMinRowsPerCta = 128;       // smallest row slab worth a CTA
 constexpr unsigned long long kSpinLimitNs = 4000000000ull;  // 4 s bound on any device-wide wait
 
 // Control block layout (int32 words, device memory, zeroed before each launch).
+// kCtlBarCount counts CTA arrivals over the whole launch (barrier k completes at k * grid).
 enum CtlWord { kCtlStatus = 0, kCtlColumn = 1, kCtlBarCount = 2, kCtlBarGen = 3, kCtlWords = 4 };
 
 // Device status codes (equal to the public mgsa_status values).
@@ -34,7 +35,7 @@ struct SweepArgs {
   int ldr;
   double* X;       // HP: m x n (x_j, then p_j); HA: x_i in column 0; naive: x_i, p_i in columns 0, 1
   int64_t ldx;
-  double* part;    // (n + 1) * G partial sums: part[j*G + b] (dots), part[n*G + b] (norm)
+  double* part;    // (2n + 1) * G partial sums: dots [parity][b][j] (two step-parity buffers), then norm [b]
   int* ctl;        // control block (CtlWord)
   int64_t rpc;     // rows per CTA, multiple of 32
   int chunk;       // rows per staged chunk, multiple of 32
@@ -43,7 +44,7 @@ struct SweepArgs {
 // Shared memory bytes the single-instance kernel needs for n columns and a chunk.
 inline size_t sweep_smem_bytes(int n, int chunk) {
   const int kmax = (n + kWarps - 1) / kWarps + 2;
-  return sizeof(double) * (size_t)(3 * chunk + kWarps * kmax + 2 * n + kWarps + 2);
+  return sizeof(double) * (size_t)(4 * chunk + kWarps * kmax + 2 * n + kThreads + 1 + 8);
 }
 
 // Records the message mgsa_last_error returns on this thread (mgsa_api.cu).

@@ -104,7 +104,7 @@ extern "C" mgsa_status mgsa_qr_noalloc(const mgsa_csr* A, const double* Z, int64
   const size_t smem = mgsa::sweep_smem_bytes(n, chunk);
   const int64_t ldx = round_up(m, 32);
   const int xcols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
-  const size_t part_bytes = (size_t)round_up((int64_t)sizeof(double) * (n + 1) * grid, 256);
+  const size_t part_bytes = (size_t)round_up((int64_t)sizeof(double) * (2 * n + 1) * grid, 256);
   const size_t x_bytes = sizeof(double) * (size_t)ldx * (size_t)xcols;
   if (kCtlBytes + part_bytes + x_bytes > kScratchBytes)
     return fail(MGSA_ERR_INVALID,

@@ -5,12 +5,13 @@
 // Every CTA owns rows [b*rpc, min(m, (b+1)*rpc)) of Z/Q and X for the whole
 // kernel.  Step i of the loop is:
 //
-//   L  (i > 0)  update column i with step i-1:  z_i -= r_{i-1,i} q_{i-1}
+//   L   (i > 0) update column i with step i-1:  z_i -= r_{i-1,i} q_{i-1}
 //               (HP also x_i -= r_{i-1,i} p_{i-1}); HP accumulates z_i^T x_i.
-//   MV  (HA, naive) x_i = A z_i  (eq. in Algorithms 4/7), accumulating z_i^T x_i.
-//   D   r_ii = sqrt(sum of partials)  (breakdown / non-finite check).
-//   MV2 (naive) p_i = A q_i  with q_i = z_i / r_ii gathered on the fly.
-//   B   q_i = z_i / r_ii (stored), p_i = x_i / r_ii (eq. (tec1)); for every
+//   MV  (HA, naive) x_i = A z_i (the per-column MV of Algorithms 4/7),
+//               accumulating z_i^T x_i.
+//   D   r_ii = sqrt(sum of partials) (breakdown / non-finite check).
+//   MV2 (naive) p_i = A q_i with q_i = z_i / r_ii gathered on the fly.
+//   F   q_i = z_i / r_ii (stored), p_i = x_i / r_ii (eq. (tec1)); for every
 //       j > i: apply step i-1's rank-1 updates z_j -= r_{i-1,j} q_{i-1}
 //       (HP: x_j -= r_{i-1,j} p_{i-1}, eq. (tec2) one term at a time) and
 //       accumulate r_ij = p_i^T z_j^{(i-1)}.
@@ -19,11 +20,38 @@
 // over the remaining columns.  Division by r_ii is a multiplication by the
 // reciprocal, formed once per step.
 //
-// Reductions are deterministic: a fixed warp-shuffle tree inside a warp, a
-// fixed order over warp pieces inside the CTA, then every CTA sums the G CTA
+// Only r_{i,i+1} is needed before the next step's first barrier; the other
+// r_ij are summed while that barrier is pending (split arrive / wait), with
+// the per-CTA partials double-buffered by step parity.
+//
+// On GB300 one warp-wide FP64 instruction holds the FP64 pipe for ~16 cycles,
+// so every FP64 operation outside the fused pass is done once (not once per
+// thread) or lane-per-column.  Reductions are deterministic: fixed trees and
+// fixed orders that do not depend on timing; every CTA sums the G per-CTA
 // partials in the same order.  Device-wide waits are bounded (kSpinLimitNs);
 // on timeout the status word is set and every CTA returns.
 #include "mgsa_internal.cuh"
+
+// Phase tracing (off unless compiled with -DMGSA_PHASE_TRACE): CTA 0 records
+// %globaltimer at the phase boundaries of every step into g_mgsa_trace, which
+// the traced build exports through mgsa_trace_fetch.  The product build
+// contains neither.
+#ifdef MGSA_PHASE_TRACE
+__device__ unsigned long long g_mgsa_trace[4200][12];
+extern "C" int mgsa_trace_fetch(unsigned long long* host) {
+  return (int)cudaMemcpyFromSymbol(host, g_mgsa_trace, sizeof(g_mgsa_trace));
+}
+#define MGSA_TRACE(step, slot)                                            \
+  do {                                                                    \
+    if (blockIdx.x == 0 && threadIdx.x == 0) {                            \
+      unsigned long long t_;                                              \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));              \
+      g_mgsa_trace[(step)][(slot)] = t_;                                  \
+    }                                                                     \
+  } while (0)
+#else
+#define MGSA_TRACE(step, slot) ((void)0)
+#endif
 
 namespace mgsa {
 
@@ -58,19 +86,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Deterministic CTA-wide sum; the result is returned to every thread.
-__device__ double block_sum(double v, double* s_red) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) s_red[warp] = v;
+// Deterministic CTA-wide sum returned to every thread: the 512 values go to
+// shared memory, lane l of warp 0 adds values l, l+32, ... in order, then a
+// butterfly.  (21 warp-wide FP64 instructions instead of 85 for 16 butterflies.)
+__device__ double block_sum(double v, double* s_buf) {
+  s_buf[threadIdx.x] = v;
   __syncthreads();
-  if (warp == 0) {
-    double t = lane < kWarps ? s_red[lane] : 0.0;
+  if (threadIdx.x < 32) {
+    double t = s_buf[threadIdx.x];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) t += s_buf[threadIdx.x + 32 * w];
     t = warp_sum(t);
-    if (lane == 0) s_red[kWarps] = t;
+    if (threadIdx.x == 0) s_buf[kThreads] = t;
   }
   __syncthreads();
-  const double r = s_red[kWarps];
+  const double r = s_buf[kThreads];
   __syncthreads();
   return r;
 }
@@ -79,25 +109,35 @@ __device__ void set_status(int* ctl, int code, int column) {
   if (atomicCAS(&ctl[kCtlStatus], 0, code) == 0) atomicExch(&ctl[kCtlColumn], column);
 }
 
-// Device-wide barrier for a cooperative launch.  Returns false if the wait
-// ran past kSpinLimitNs or another CTA already recorded a failure.
-__device__ bool grid_sync(int* ctl, unsigned int& gen) {
-  __shared__ int s_ok;
+// Device-wide barrier for a cooperative launch, in two halves so that a CTA
+// can do independent work between arriving and waiting.  The counter only
+// grows during a launch (it is zeroed before each launch): barrier number k
+// (k = 1, 2, ...) is passed once it reaches k * gridDim.x.  Arrival is a
+// fire-and-forget release reduction; every CTA then polls the counter with
+// acquire loads.  Only thread 0 of a CTA touches it; `gen` (the number of
+// barriers passed) is meaningful in thread 0 only.
+__device__ __forceinline__ void grid_arrive(int* ctl, unsigned int gen, int* s_unused) {
+  (void)gen;
+  (void)s_unused;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int* count = reinterpret_cast<unsigned int*>(&ctl[kCtlBarCount]);
-    unsigned int* genp = reinterpret_cast<unsigned int*>(&ctl[kCtlBarGen]);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+  }
+}
+
+// Returns false if the wait ran past kSpinLimitNs or another CTA already
+// recorded a failure (then every CTA leaves the kernel).
+__device__ bool grid_wait(int* ctl, unsigned int& gen, const int* s_unused, int* s_ok) {
+  (void)s_unused;
+  if (threadIdx.x == 0) {
+    const unsigned int* count = reinterpret_cast<const unsigned int*>(&ctl[kCtlBarCount]);
+    const unsigned int target = (gen + 1u) * gridDim.x;
     int ok = 1;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicExch(genp, gen + 1u);
-    } else {
+    if (ld_acquire_u32(count) < target) {
       const unsigned long long t0 = global_timer_ns();
       unsigned int polls = 0;
-      while (ld_acquire_u32(genp) == gen) {
+      while (ld_acquire_u32(count) < target) {
         if ((++polls & 255u) == 0u) {
           if (ld_relaxed_i32(&ctl[kCtlStatus]) != 0) { ok = 0; break; }
           if (global_timer_ns() - t0 > kSpinLimitNs) {
@@ -108,48 +148,231 @@ __device__ bool grid_sync(int* ctl, unsigned int& gen) {
         }
       }
     }
-    __threadfence();
     gen += 1u;
-    s_ok = ok;
+    *s_ok = ok;
   }
   __syncthreads();
-  return s_ok != 0;
+  return *s_ok != 0;
 }
 
-// Sum of the G per-CTA partials part[0..G), same order in every CTA.
-__device__ double reduce_ctas(const double* part, int G, double* s_red) {
+__device__ __forceinline__ bool grid_sync(int* ctl, unsigned int& gen, int* s_flags) {
+  grid_arrive(ctl, gen, s_flags);
+  return grid_wait(ctl, gen, s_flags, s_flags + 1);
+}
+
+// Sum over CTAs b (in order of b, fixed tree) of part[b * stride], by warp 0;
+// lane 0 returns the sum.
+__device__ __forceinline__ double warp0_sum_ctas(const double* part, int64_t stride, int G) {
+  double t = 0.0;
+  for (int b0 = 0; b0 < G; b0 += 160) {
+    double v[5];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      const int bb = b0 + (int)threadIdx.x + 32 * s;
+      v[s] = bb < G ? ld_cg(part + bb * stride) : 0.0;
+    }
+    t += (((v[0] + v[1]) + v[2]) + v[3]) + v[4];
+  }
+  return warp_sum(t);
+}
+
+// r_ii from the norm partials: one thread forms the sum's square root, its
+// reciprocal and the breakdown verdict and broadcasts them.
+// s_scal[0] = r_ii, s_scal[1] = 1/r_ii, s_scal[2] = status (0 ok).
+__device__ void diagonal(const double* part_norm, int G, double* s_scal) {
   if (threadIdx.x < 32) {
-    double t = 0.0;
-    for (int bb = threadIdx.x; bb < G; bb += 32) t += ld_cg(part + bb);
-    t = warp_sum(t);
-    if (threadIdx.x == 0) s_red[kWarps + 1] = t;
+    const double stot = warp0_sum_ctas(part_norm, 1, G);
+    if (threadIdx.x == 0) {
+      int st = kDevOk;
+      double r = 0.0, inv = 0.0;
+      if (isnan(stot) || isinf(stot)) st = kDevNonfinite;
+      else if (!(stot > 0.0)) st = kDevBreakdown;
+      else {
+        r = sqrt(stot);
+        inv = 1.0 / r;
+      }
+      s_scal[0] = r;
+      s_scal[1] = inv;
+      s_scal[2] = (double)st;
+    }
   }
   __syncthreads();
-  const double r = s_red[kWarps + 1];
+}
+
+// r_{i,i+1}: the first entry of row i right of the diagonal (warp 0).
+__device__ void reduce_first(const double* part, int G, int n, int i, double* s_rrow, double* R, int ldr,
+                             bool write_r) {
+  if (threadIdx.x < 32) {
+    const double r = warp0_sum_ctas(part + (i + 1), n, G);
+    if (threadIdx.x == 0) {
+      s_rrow[i + 1] = r;
+      if (write_r) R[i + (int64_t)(i + 1) * ldr] = r;
+    }
+  }
   __syncthreads();
-  return r;
+}
+
+// r_ij for j = i+2 .. n-1, lane per column: warp w adds the partials of the
+// CTAs in [w*G/16, (w+1)*G/16) in order, then warp 0 adds the 16 warp sums in
+// order.  Loads are coalesced because part is laid out [CTA][column].
+__device__ void reduce_rest(const double* part, int G, int n, int i, double* s_rrow, double* s_buf, double* R,
+                            int ldr, bool write_r) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int bb0 = (int)((int64_t)G * warp / kWarps), bb1 = (int)((int64_t)G * (warp + 1) / kWarps);
+  for (int j0 = i + 2; j0 < n; j0 += 32) {
+    const int j = j0 + lane;
+    double t0 = 0.0, t1 = 0.0;
+    int bb = bb0;
+    for (; bb + 1 < bb1; bb += 2) {
+      const double v0 = j < n ? ld_cg(part + (int64_t)bb * n + j) : 0.0;
+      const double v1 = j < n ? ld_cg(part + (int64_t)(bb + 1) * n + j) : 0.0;
+      t0 += v0;
+      t1 += v1;
+    }
+    if (bb < bb1) t0 += j < n ? ld_cg(part + (int64_t)bb * n + j) : 0.0;
+    s_buf[threadIdx.x] = t0 + t1;
+    __syncthreads();
+    if (warp == 0 && j < n) {
+      double t = s_buf[lane];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) t += s_buf[lane + 32 * w];
+      s_rrow[j] = t;
+      if (write_r) R[i + (int64_t)j * ldr] = t;
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int kTripRows = 8;                     // rows per lane per trip of the fused pass
+constexpr int kResRows = kMaxChunk / kThreads;  // rows per thread when a CTA's slab is one chunk
+
+// out[q] = sum_e val[e] * (scale_src ? src[col[e]] * scale : src[col[e]]) for
+// the rows k + q*kThreads (q < 4) below k1, each summed in stored order.  The
+// four rows advance in lockstep so their gathers are in flight together.
+__device__ __forceinline__ void csr_rows4(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                          const double* __restrict__ val, const double* src, double scale,
+                                          bool scale_src, int64_t k, int64_t k1, double out[4]) {
+  int e[4], e1[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t kk = k + q * kThreads;
+    e[q] = kk < k1 ? __ldg(rowptr + kk) : 0;
+    e1[q] = kk < k1 ? __ldg(rowptr + kk + 1) : 0;
+    out[q] = 0.0;
+  }
+  while (e[0] < e1[0] || e[1] < e1[1] || e[2] < e1[2] || e[3] < e1[3]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (e[q] < e1[q]) {
+        const double zv = ld_cg(src + __ldg(colidx + e[q]));
+        out[q] = fma(__ldg(val + e[q]), scale_src ? zv * scale : zv, out[q]);
+        ++e[q];
+      }
+    }
+  }
+}
+
+// The fused pass over one chunk of rows [c0, c0 + crows) and the columns
+// j = i+1 .. n-1: apply step i-1's updates z_j -= r_{i-1,j} q_{i-1} (HP:
+// x_j -= r_{i-1,j} p_{i-1}) and accumulate p_i^T z_j.  Work units are
+// (column, 32-row block) pairs split into equal contiguous ranges, one per
+// warp; each warp reduces each of its column pieces with a butterfly and the
+// pieces are added in warp order into s_racc.  Pivots come from shared
+// memory: s_qprev = q_{i-1}, s_pprev = p_{i-1}, s_pcur = p_i.
+template <int V>
+__device__ __forceinline__ void fused_pass(int i, int n, int64_t c0, int crows, const double* s_qprev,
+                                           const double* s_pprev, const double* s_pcur, const double* s_rrow,
+                                           double* __restrict__ Q, int64_t ldq, double* __restrict__ X, int64_t ldx,
+                                           double* s_piece, int kmax, int* s_wfirst, int* s_wlast, double* s_racc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ncols = n - 1 - i;
+  const int nb = (crows + 31) >> 5;
+  const int U = ncols * nb;  // <= 2047 * 128
+  int u = (int)((int64_t)U * warp / kWarps);
+  const int u1 = (int)((int64_t)U * (warp + 1) / kWarps);
+  const int jfirst = u / nb;
+  if (lane == 0) {
+    s_wfirst[warp] = u < u1 ? jfirst : (1 << 30);
+    s_wlast[warp] = u < u1 ? (u1 - 1) / nb : -1;
+  }
+  while (u < u1) {
+    const int jr = u / nb;
+    const int j = i + 1 + jr;
+    const int uend = (jr + 1) * nb < u1 ? (jr + 1) * nb : u1;
+    const double rp = (i > 0) ? s_rrow[j] : 0.0;
+    double* zc = Q + (int64_t)j * ldq + c0;
+    double* xc = (V == kHP) ? X + (int64_t)j * ldx + c0 : X;
+    double acc0 = 0.0, acc1 = 0.0;
+    const int rbeg = (u - jr * nb) * 32 + lane;
+    int rend = (uend - jr * nb) * 32;
+    if (rend > crows) rend = crows;
+    // kTripRows rows per lane per trip: every load of the trip is issued
+    // before its arithmetic, so each lane keeps that many requests in flight.
+    for (int r = rbeg; r < rend; r += 32 * kTripRows) {
+      double z[kTripRows], x[kTripRows];
+#pragma unroll
+      for (int q = 0; q < kTripRows; ++q) {
+        const int rr = r + 32 * q;
+        z[q] = rr < rend ? zc[rr] : 0.0;
+        x[q] = (V == kHP && i > 0 && rr < rend) ? xc[rr] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < kTripRows; ++q) {
+        const int rr = r + 32 * q;
+        if (rr < rend) {
+          if (i > 0) {
+            z[q] = fma(-rp, s_qprev[rr], z[q]);
+            zc[rr] = z[q];
+            if (V == kHP) xc[rr] = fma(-rp, s_pprev[rr], x[q]);
+          }
+          if (q & 1) acc1 = fma(s_pcur[rr], z[q], acc1);
+          else acc0 = fma(s_pcur[rr], z[q], acc0);
+        }
+      }
+    }
+    const double acc = warp_sum(acc0 + acc1);
+    if (lane == 0) s_piece[warp * kmax + (jr - jfirst)] = acc;
+    u = uend;
+  }
+  __syncthreads();
+  MGSA_TRACE(i, 5);
+  // Combine the warp pieces of each column in warp order.
+  for (int jr = threadIdx.x; jr < ncols; jr += kThreads) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w)
+      if (jr >= s_wfirst[w] && jr <= s_wlast[w]) t += s_piece[w * kmax + (jr - s_wfirst[w])];
+    s_racc[jr] += t;
+  }
+  __syncthreads();
 }
 
 template <int V>
 __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(16) double smem[];
+  __shared__ int s_wfirst[kWarps], s_wlast[kWarps];
+  __shared__ int s_flags[2];
   const int n = a.n;
   const int chunk = a.chunk;
   const int kmax = (n + kWarps - 1) / kWarps + 2;
-  double* s_qprev = smem;                    // q_{i-1} for the chunk rows
-  double* s_pprev = s_qprev + chunk;         // p_{i-1} (HP)
-  double* s_pcur = s_pprev + chunk;          // p_i
-  double* s_piece = s_pcur + chunk;          // kWarps x kmax warp pieces
+  double* s_piv = smem;                      // 4 x chunk pivot rows
+  double* s_piece = s_piv + 4 * chunk;       // kWarps x kmax warp pieces
   double* s_racc = s_piece + kWarps * kmax;  // CTA partials of the current row (relative column)
   double* s_rrow = s_racc + n;               // r_{i-1, j} during step i, then r_{i, j}
-  double* s_red = s_rrow + n;                // kWarps + 2 scratch
+  double* s_buf = s_rrow + n;                // kThreads + 1 reduction scratch
+  double* s_scal = s_buf + kThreads + 1;     // r_ii, 1/r_ii, status
 
   const int G = gridDim.x;
   const int b = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int64_t m = a.m;
   const int64_t k0 = (int64_t)b * a.rpc;
   const int64_t k1 = (k0 + a.rpc < m) ? k0 + a.rpc : m;
+  const int crows_all = (int)(k1 - k0);
+  // Resident mode: every slab is one chunk, so a CTA keeps q_{i-1}, p_{i-1}
+  // in shared memory from one step to the next and its rows of z_i, x_i in
+  // registers between the diagonal and the fused pass.
+  const bool resident = a.rpc <= chunk;
   const int32_t* __restrict__ rowptr = a.rowptr;
   const int32_t* __restrict__ colidx = a.col;
   const double* __restrict__ val = a.val;
@@ -159,11 +382,13 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
   double* __restrict__ R = a.R;
   const int64_t ldz = a.ldz, ldq = a.ldq, ldx = a.ldx;
   const int ldr = a.ldr;
-  double* part_norm = a.part + (int64_t)n * G;
+  // part: two buffers (step parity) of G x n dot partials, then G norm partials.
+  double* part_norm = a.part + 2 * (int64_t)n * G;
   unsigned int gen = 0;
 
+  MGSA_TRACE(4100, 0);
   // ---- Phase 0: R = 0; Q = Z on own rows; HP: X = A Z (one block product,
-  // Algorithm 8 first line) and the partial z_1^T x_1. ----
+  // Algorithm 8 first line) and, outside resident mode, the partial z_1^T x_1. ----
   if (b == 0) {
     for (int64_t t = tid; t < (int64_t)n * n; t += kThreads) R[(t % n) + (t / n) * ldr] = 0.0;
   }
@@ -194,187 +419,303 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
         }
       }
     }
-    s0 = block_sum(s0, s_red);
-    if (tid == 0) part_norm[b] = s0;
+    if (!resident) {
+      s0 = block_sum(s0, s_buf);
+      if (tid == 0) part_norm[b] = s0;
+    }
   } else {
     for (int j = 0; j < n; ++j)
       for (int64_t k = k0 + tid; k < k1; k += kThreads) Q[k + (int64_t)j * ldq] = __ldg(Z + k + (int64_t)j * ldz);
   }
+  __syncthreads();
+  MGSA_TRACE(4100, 1);
 
   for (int i = 0; i < n; ++i) {
-    // ---------------- diagonal: r_ii = sqrt(z_i^T x_i) ----------------
+    MGSA_TRACE(i, 0);
+    const int cur = i & 1, prev = cur ^ 1;
+    double* zi = Q + (int64_t)i * ldq;
+    const double* part_prev = a.part + (int64_t)prev * n * G;  // partials of row i-1
+    double* part_cur = a.part + (int64_t)cur * n * G;          // partials of row i
+    // This thread's rows tid + t*kThreads of z_i and x_i (naive: p_i), resident mode only.
+    double zr[kResRows], xr[kResRows];
+    // ---------------- column i: r_ii = sqrt(z_i^T x_i) ----------------
     if (V == kHP) {
-      if (i > 0) {
+      if (resident) {
+        const double r = (i > 0) ? s_rrow[i] : 0.0;  // r_{i-1,i}
+        const double* xi = X + (int64_t)i * ldx;
+        const double* sq = s_piv + 2 * prev * chunk;
+        const double* sp = sq + chunk;
+#pragma unroll
+        for (int t = 0; t < kResRows; ++t) {
+          const int rr = tid + t * kThreads;
+          zr[t] = rr < crows_all ? zi[k0 + rr] : 0.0;
+          xr[t] = rr < crows_all ? xi[k0 + rr] : 0.0;
+        }
+        double sl = 0.0;
+#pragma unroll
+        for (int t = 0; t < kResRows; ++t) {
+          const int rr = tid + t * kThreads;
+          if (rr < crows_all) {
+            if (i > 0) {
+              zr[t] = fma(-r, sq[rr], zr[t]);
+              xr[t] = fma(-r, sp[rr], xr[t]);
+            }
+            sl = fma(zr[t], xr[t], sl);
+          }
+        }
+        sl = block_sum(sl, s_buf);
+        if (tid == 0) part_norm[b] = sl;
+      } else if (i > 0) {
         const double r = s_rrow[i];  // r_{i-1,i}
         double sl = 0.0;
-        double* zi = Q + (int64_t)i * ldq;
         double* xi = X + (int64_t)i * ldx;
         const double* qp = Q + (int64_t)(i - 1) * ldq;
         const double* pp = X + (int64_t)(i - 1) * ldx;
-        for (int64_t k = k0 + tid; k < k1; k += kThreads) {
-          const double z = fma(-r, qp[k], zi[k]);
-          const double x = fma(-r, pp[k], xi[k]);
-          zi[k] = z;
-          xi[k] = x;
-          sl = fma(z, x, sl);
+        // Four rows per thread per trip, loads first (rows stay in ascending order).
+        for (int64_t k = k0 + tid; k < k1; k += 4 * kThreads) {
+          double zz[4], xx[4], qq[4], pv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int64_t kk = k + q * kThreads;
+            const bool ok = kk < k1;
+            zz[q] = ok ? zi[kk] : 0.0;
+            xx[q] = ok ? xi[kk] : 0.0;
+            qq[q] = ok ? qp[kk] : 0.0;
+            pv[q] = ok ? pp[kk] : 0.0;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int64_t kk = k + q * kThreads;
+            if (kk < k1) {
+              const double z = fma(-r, qq[q], zz[q]);
+              const double x = fma(-r, pv[q], xx[q]);
+              zi[kk] = z;
+              xi[kk] = x;
+              sl = fma(z, x, sl);
+            }
+          }
         }
-        sl = block_sum(sl, s_red);
+        sl = block_sum(sl, s_buf);
         if (tid == 0) part_norm[b] = sl;
       }
-      if (!grid_sync(a.ctl, gen)) return;
+      MGSA_TRACE(i, 1);
+      grid_arrive(a.ctl, gen, s_flags);
+      if (i > 0) reduce_rest(part_prev, G, n, i - 1, s_rrow, s_buf, R, ldr, b == 0);  // r_{i-1,j}, j > i
+      if (!grid_wait(a.ctl, gen, s_flags, s_flags + 1)) return;
     } else {
       const double* zsrc;  // column i of the working Z, complete on every row
       if (i > 0) {
         const double r = s_rrow[i];
-        double* zi = Q + (int64_t)i * ldq;
         const double* qp = Q + (int64_t)(i - 1) * ldq;
-        for (int64_t k = k0 + tid; k < k1; k += kThreads) zi[k] = fma(-r, qp[k], zi[k]);
-        if (!grid_sync(a.ctl, gen)) return;
+        if (resident) {
+          const double* sq = s_piv + 2 * prev * chunk;
+#pragma unroll
+          for (int t = 0; t < kResRows; ++t) {
+            const int rr = tid + t * kThreads;
+            zr[t] = rr < crows_all ? zi[k0 + rr] : 0.0;
+          }
+#pragma unroll
+          for (int t = 0; t < kResRows; ++t) {
+            const int rr = tid + t * kThreads;
+            if (rr < crows_all) {
+              zr[t] = fma(-r, sq[rr], zr[t]);
+              zi[k0 + rr] = zr[t];
+            }
+          }
+        } else {
+          for (int64_t k = k0 + tid; k < k1; k += 4 * kThreads) {
+            double zz[4], qq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int64_t kk = k + q * kThreads;
+              zz[q] = kk < k1 ? zi[kk] : 0.0;
+              qq[q] = kk < k1 ? qp[kk] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int64_t kk = k + q * kThreads;
+              if (kk < k1) zi[kk] = fma(-r, qq[q], zz[q]);
+            }
+          }
+        }
+        grid_arrive(a.ctl, gen, s_flags);
+        reduce_rest(part_prev, G, n, i - 1, s_rrow, s_buf, R, ldr, b == 0);  // r_{i-1,j}, j > i
+        if (!grid_wait(a.ctl, gen, s_flags, s_flags + 1)) return;
         zsrc = zi;
       } else {
         zsrc = Z;  // column 0 of the input equals the working column 0
+        if (resident) {
+#pragma unroll
+          for (int t = 0; t < kResRows; ++t) {
+            const int rr = tid + t * kThreads;
+            zr[t] = rr < crows_all ? __ldg(Z + k0 + rr) : 0.0;
+          }
+        }
       }
       // x_i = A z_i^{(i-1)}  (Algorithm 4/7: the per-column MV)
       double sl = 0.0;
-      for (int64_t k = k0 + tid; k < k1; k += kThreads) {
-        const int e0 = __ldg(rowptr + k), e1 = __ldg(rowptr + k + 1);
-        double x = 0.0;
-        for (int e = e0; e < e1; ++e) x = fma(__ldg(val + e), ld_cg(zsrc + __ldg(colidx + e)), x);
-        X[k] = x;
-        sl = fma(ld_cg(zsrc + k), x, sl);
+      if (resident) {
+#pragma unroll
+        for (int h = 0; h < kResRows / 4; ++h) {
+          double xv[4];
+          csr_rows4(rowptr, colidx, val, zsrc, 1.0, false, k0 + tid + (int64_t)h * 4 * kThreads, k1, xv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xr[4 * h + q] = xv[q];
+        }
+#pragma unroll
+        for (int t = 0; t < kResRows; ++t)
+          if (tid + t * kThreads < crows_all) sl = fma(zr[t], xr[t], sl);
+      } else {
+        for (int64_t k = k0 + tid; k < k1; k += 4 * kThreads) {
+          double xv[4], zk[4];
+          csr_rows4(rowptr, colidx, val, zsrc, 1.0, false, k, k1, xv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int64_t kk = k + q * kThreads;
+            zk[q] = kk < k1 ? ld_cg(zsrc + kk) : 0.0;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int64_t kk = k + q * kThreads;
+            if (kk < k1) {
+              X[kk] = xv[q];
+              sl = fma(zk[q], xv[q], sl);
+            }
+          }
+        }
       }
-      sl = block_sum(sl, s_red);
+      sl = block_sum(sl, s_buf);
       if (tid == 0) part_norm[b] = sl;
-      if (!grid_sync(a.ctl, gen)) return;
+      MGSA_TRACE(i, 1);
+      if (!grid_sync(a.ctl, gen, s_flags)) return;
     }
-    const double stot = reduce_ctas(part_norm, G, s_red);
-    if (!(stot > 0.0) || isinf(stot)) {
-      if (b == 0 && tid == 0) set_status(a.ctl, (isnan(stot) || isinf(stot)) ? kDevNonfinite : kDevBreakdown, i + 1);
+    MGSA_TRACE(i, 2);
+    diagonal(part_norm, G, s_scal);
+    MGSA_TRACE(i, 3);
+    if (s_scal[2] != 0.0) {
+      if (b == 0 && tid == 0) set_status(a.ctl, (int)s_scal[2], i + 1);
       return;  // every CTA took the same decision from the same sum
     }
-    const double rii = sqrt(stot);
-    const double inv = 1.0 / rii;
-    if (b == 0 && tid == 0) R[i + (int64_t)i * ldr] = rii;
+    const double inv = s_scal[1];
+    if (b == 0 && tid == 0) R[i + (int64_t)i * ldr] = s_scal[0];
 
     if (V == kNaive) {
       // p_i = A q_i with q_i = z_i / r_ii formed on the fly (Algorithm 4's second MV).
-      const double* zsrc = (i > 0) ? Q + (int64_t)i * ldq : Z;
-      for (int64_t k = k0 + tid; k < k1; k += kThreads) {
-        const int e0 = __ldg(rowptr + k), e1 = __ldg(rowptr + k + 1);
-        double p = 0.0;
-        for (int e = e0; e < e1; ++e) p = fma(__ldg(val + e), ld_cg(zsrc + __ldg(colidx + e)) * inv, p);
-        X[k + ldx] = p;
+      const double* zsrc = (i > 0) ? zi : Z;
+      if (resident) {
+#pragma unroll
+        for (int h = 0; h < kResRows / 4; ++h) {
+          double pv[4];
+          csr_rows4(rowptr, colidx, val, zsrc, inv, true, k0 + tid + (int64_t)h * 4 * kThreads, k1, pv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xr[4 * h + q] = pv[q];
+        }
+      } else {
+        for (int64_t k = k0 + tid; k < k1; k += 4 * kThreads) {
+          double pv[4];
+          csr_rows4(rowptr, colidx, val, zsrc, inv, true, k, k1, pv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int64_t kk = k + q * kThreads;
+            if (kk < k1) X[kk + ldx] = pv[q];
+          }
+        }
       }
       // Other CTAs still gather z_i; q_i may overwrite it only after this wait.
-      if (!grid_sync(a.ctl, gen)) return;
+      if (!grid_sync(a.ctl, gen, s_flags)) return;
     }
 
-    // ---------------- B pass ----------------
+    // ---------------- fused pass ----------------
     const int ncols = n - 1 - i;
     for (int jr = tid; jr < ncols; jr += kThreads) s_racc[jr] = 0.0;
-    double* const zi = Q + (int64_t)i * ldq;
-    const double* const qprev = Q + (int64_t)(i > 0 ? i - 1 : 0) * ldq;
-    const double* const pprev = (V == kHP) ? X + (int64_t)(i > 0 ? i - 1 : 0) * ldx : X;
-    for (int64_t c0 = k0; c0 < k1; c0 += chunk) {
-      const int crows = (int)((k1 - c0) < chunk ? (k1 - c0) : chunk);
-      const int nb = (crows + 31) >> 5;
-      // Stage the pivots: q_i, p_i are formed (and stored), q_{i-1}, p_{i-1} loaded.
-      for (int r = tid; r < nb * 32; r += kThreads) {
-        double pc = 0.0, qp = 0.0, pp = 0.0;
-        if (r < crows) {
-          const int64_t k = c0 + r;
-          zi[k] = zi[k] * inv;  // q_i = z_i / r_ii
-          if (V == kHP) {
-            pc = X[k + (int64_t)i * ldx] * inv;  // p_i = x_i / r_ii (eq. (tec1))
-            X[k + (int64_t)i * ldx] = pc;
-          } else if (V == kHA) {
-            pc = X[k] * inv;
-          } else {
-            pc = X[k + ldx];
+    if (resident) {
+      // q_i = z_i / r_ii and p_i (eq. (tec1); naive: A q_i) from registers into
+      // global memory and into this step's half of the pivot buffer.
+      double* sqc = s_piv + 2 * cur * chunk;
+      double* spc = sqc + chunk;
+      const int nb32 = ((crows_all + 31) >> 5) * 32;
+#pragma unroll
+      for (int t = 0; t < kResRows; ++t) {
+        const int rr = tid + t * kThreads;
+        if (rr < nb32) {
+          double qv = 0.0, pv = 0.0;
+          if (rr < crows_all) {
+            qv = zr[t] * inv;
+            zi[k0 + rr] = qv;
+            pv = (V == kNaive) ? xr[t] : xr[t] * inv;
+            if (V == kHP) X[k0 + rr + (int64_t)i * ldx] = pv;
           }
-          if (i > 0) {
-            qp = qprev[k];
-            if (V == kHP) pp = pprev[k];
-          }
+          sqc[rr] = qv;
+          spc[rr] = pv;
         }
-        s_pcur[r] = pc;
-        s_qprev[r] = qp;
-        s_pprev[r] = pp;
       }
       __syncthreads();
-      const int64_t U = (int64_t)ncols * nb;  // work units: (column, 32-row block)
+      MGSA_TRACE(i, 4);
       if (ncols > 0) {
-        int64_t u = U * warp / kWarps;
-        const int64_t u1 = U * (warp + 1) / kWarps;
-        const int jfirst = (int)(u / nb);
-        while (u < u1) {
-          const int jr = (int)(u / nb);
-          const int j = i + 1 + jr;
-          const int64_t uend = ((int64_t)(jr + 1) * nb < u1) ? (int64_t)(jr + 1) * nb : u1;
-          const double rp = (i > 0) ? s_rrow[j] : 0.0;
-          double* zc = Q + (int64_t)j * ldq + c0;
-          double* xc = (V == kHP) ? X + (int64_t)j * ldx + c0 : X;
-          double acc = 0.0;
-          const int rbeg = (int)(u - (int64_t)jr * nb) * 32 + lane;
-          int rend = (int)(uend - (int64_t)jr * nb) * 32;
-          if (rend > crows) rend = crows;
-          // Four rows per lane per trip: all loads are issued before the
-          // arithmetic so each lane keeps several requests in flight.
-          for (int r = rbeg; r < rend; r += 128) {
-            double z[4], x[4];
+        const double* sqp = s_piv + 2 * prev * chunk;
+        fused_pass<V>(i, n, k0, crows_all, sqp, sqp + chunk, spc, s_rrow, Q, ldq, X, ldx, s_piece, kmax, s_wfirst,
+                      s_wlast, s_racc);
+      }
+    } else {
+      double* s_qprev = s_piv;
+      double* s_pprev = s_piv + chunk;
+      double* s_pcur = s_piv + 2 * chunk;
+      const double* const qprev = Q + (int64_t)(i > 0 ? i - 1 : 0) * ldq;
+      const double* const pprev = (V == kHP) ? X + (int64_t)(i > 0 ? i - 1 : 0) * ldx : X;
+      const double* xsrc = (V == kHP) ? X + (int64_t)i * ldx : (V == kHA ? X : X + ldx);
+      for (int64_t c0 = k0; c0 < k1; c0 += chunk) {
+        const int crows = (int)((k1 - c0) < chunk ? (k1 - c0) : chunk);
+        const int nb = (crows + 31) >> 5;
+        // Stage the pivots: q_i, p_i are formed (and stored), q_{i-1}, p_{i-1}
+        // loaded.  Four rows per thread per trip, loads first.
+        for (int r0 = tid; r0 < nb * 32; r0 += 4 * kThreads) {
+          double zv[4], xv[4], qv[4], pv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int rr = r + 32 * q;
-              z[q] = rr < rend ? zc[rr] : 0.0;
-              x[q] = (V == kHP && i > 0 && rr < rend) ? xc[rr] : 0.0;
-            }
+          for (int q = 0; q < 4; ++q) {
+            const int r = r0 + q * kThreads;
+            const bool ok = r < crows;
+            const int64_t k = c0 + r;
+            zv[q] = ok ? zi[k] : 0.0;
+            xv[q] = ok ? xsrc[k] : 0.0;
+            qv[q] = (ok && i > 0) ? qprev[k] : 0.0;
+            pv[q] = (ok && i > 0 && V == kHP) ? pprev[k] : 0.0;
+          }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int rr = r + 32 * q;
-              if (rr < rend) {
-                if (i > 0) {
-                  z[q] = fma(-rp, s_qprev[rr], z[q]);
-                  zc[rr] = z[q];
-                  if (V == kHP) xc[rr] = fma(-rp, s_pprev[rr], x[q]);
+          for (int q = 0; q < 4; ++q) {
+            const int r = r0 + q * kThreads;
+            if (r < nb * 32) {
+              double pc = 0.0;
+              if (r < crows) {
+                const int64_t k = c0 + r;
+                zi[k] = zv[q] * inv;  // q_i = z_i / r_ii
+                if (V == kNaive) {
+                  pc = xv[q];  // p_i = A q_i from the second MV
+                } else {
+                  pc = xv[q] * inv;  // p_i = x_i / r_ii (eq. (tec1))
+                  if (V == kHP) X[k + (int64_t)i * ldx] = pc;
                 }
-                acc = fma(s_pcur[rr], z[q], acc);
               }
+              s_pcur[r] = pc;
+              s_qprev[r] = qv[q];
+              s_pprev[r] = pv[q];
             }
           }
-          acc = warp_sum(acc);
-          if (lane == 0) s_piece[warp * kmax + (jr - jfirst)] = acc;
-          u = uend;
         }
+        __syncthreads();
+        MGSA_TRACE(i, 4);
+        if (ncols > 0)
+          fused_pass<V>(i, n, c0, crows, s_qprev, s_pprev, s_pcur, s_rrow, Q, ldq, X, ldx, s_piece, kmax, s_wfirst,
+                        s_wlast, s_racc);
       }
-      __syncthreads();
-      // Combine the warp pieces of each column in warp order.
-      for (int jr = tid; jr < ncols; jr += kThreads) {
-        double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) {
-          const int64_t w0 = U * w / kWarps, w1 = U * (w + 1) / kWarps;
-          if (w0 >= w1) continue;
-          const int jf = (int)(w0 / nb), jl = (int)((w1 - 1) / nb);
-          if (jr >= jf && jr <= jl) t += s_piece[w * kmax + (jr - jf)];
-        }
-        s_racc[jr] += t;
-      }
-      __syncthreads();
     }
+    MGSA_TRACE(i, 6);
     if (ncols == 0) break;
-    for (int jr = tid; jr < ncols; jr += kThreads) a.part[(int64_t)(i + 1 + jr) * G + b] = s_racc[jr];
-    if (!grid_sync(a.ctl, gen)) return;
-    // r_ij for j > i: the same fixed-order sum over CTAs in every CTA.
-    for (int jr = warp; jr < ncols; jr += kWarps) {
-      const double* pp = a.part + (int64_t)(i + 1 + jr) * G;
-      double t = 0.0;
-      for (int bb = lane; bb < G; bb += 32) t += ld_cg(pp + bb);
-      t = warp_sum(t);
-      if (lane == 0) {
-        s_rrow[i + 1 + jr] = t;
-        if (b == 0) R[i + (int64_t)(i + 1 + jr) * ldr] = t;
-      }
-    }
-    __syncthreads();
+    for (int jr = tid; jr < ncols; jr += kThreads) part_cur[(int64_t)b * n + (i + 1 + jr)] = s_racc[jr];
+    MGSA_TRACE(i, 7);
+    if (!grid_sync(a.ctl, gen, s_flags)) return;
+    MGSA_TRACE(i, 8);
+    reduce_first(part_cur, G, n, i, s_rrow, R, ldr, b == 0);  // r_{i,i+1}; the rest waits for the next barrier
+    MGSA_TRACE(i, 9);
   }
 }
 

@@ -138,6 +138,55 @@ mgsa_status mgsa_qr_host(mgsa_handle h, const int32_t* rowptr, const int32_t* co
                          int64_t nnz, const double* Z, int64_t m, int n, int64_t ldz, mgsa_variant v,
                          double* Q, int64_t ldq, double* R, int ldr, mgsa_stream_t s, int* info);
 
+/* ---------------------------------------------------------------------- */
+/* Batched QR: many independent instances in one call.                      */
+/* ---------------------------------------------------------------------- */
+
+/* One instance of a batch.  An array of these lives in DEVICE memory and is
+ * read by the kernels (the host never dereferences it).  Every pointer is
+ * device memory owned by the caller; A, Z, Q, R, ld* and variant mean what
+ * they mean for mgsa_qr (rowptr/col/val form the CSR of the m x m SPD A).
+ * work: mgsa_job_workspace_bytes(m, n, variant) bytes used by this job only. */
+typedef struct {
+  int64_t m;
+  int32_t n;
+  int32_t variant;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const double* Z;
+  int64_t ldz;
+  double* Q;
+  int64_t ldq;
+  double* R;
+  int64_t ldr;
+  double* work;
+} mgsa_job;
+
+/* Largest n of a batched job. */
+#define MGSA_BATCH_MAX_N 256
+/* info value of a job that failed the device-side checks (bad sizes,
+ * NULL pointer, unknown variant); its outputs are untouched. */
+#define MGSA_BATCH_INFO_INVALID (-2147483647)
+
+/* Device workspace bytes one batched job of (m, n, v) needs (x / p columns):
+ * 8 * round_up(m, 32) * (n for HP, 1 for HA, 2 for naive). */
+size_t mgsa_job_workspace_bytes(int64_t m, int n, mgsa_variant v);
+
+/* QR of `count` independent instances (Section 1, eq. (1); the same
+ * right-looking Algorithms 4, 7, 8 as mgsa_qr) in one call on stream s.
+ * Persistent kernels (one per variant) take jobs from a device work queue:
+ * each CTA runs a whole instance with CTA-wide barriers, so instances of
+ * different sizes run side by side and larger ones should come first in the
+ * array for the best load balance.  info_dev[k] (device, count int32) gets 0,
+ * the 1-based breakdown column j (z_j^T x_j <= 0), -j (not finite) or
+ * MGSA_BATCH_INFO_INVALID.  The call allocates nothing and launches plain
+ * kernels (no cooperative launch), so it can be captured into a CUDA graph.
+ * Results are deterministic per instance; they may differ in the last bits
+ * from mgsa_qr's (different reduction tree).  Returns MGSA_ERR_INVALID for
+ * count < 0 or NULL arrays (count > 0); count == 0 does nothing. */
+mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, int* info_dev, mgsa_stream_t s);
+
 /* Launch parameters of the single-instance kernel (0 restores the default).
  *   MGSA_PARAM_MAX_CTAS          cap on the number of CTAs (default: one per
  *                                SM that fits, i.e. the co-resident maximum)

@@ -1,6 +1,7 @@
 // C-ABI of libmgsa: handle, argument checks, workspace and launches.
 // The numerical work is done by the kernels in mgsa_sweep.cu.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 
 #include "mgsa.h"
@@ -17,7 +18,13 @@ struct mgsa_context {
   int64_t max_ctas = 0;        // MGSA_PARAM_MAX_CTAS (0 = co-resident maximum)
   int chunk_rows = 0;          // MGSA_PARAM_CHUNK_ROWS (0 = kMaxChunk)
   int64_t min_rows = 0;        // MGSA_PARAM_MIN_ROWS_PER_CTA (0 = kMinRowsPerCta)
+  double* batch_scratch = nullptr;  // per-CTA partial sums of the batched kernels
+  int batch_grid = 0;               // CTAs of a batched launch
+  size_t batch_smem = 0;
 };
+
+static_assert(sizeof(mgsa_job) == sizeof(mgsa::BatchJob), "mgsa_job and BatchJob must match");
+static_assert(offsetof(mgsa_job, work) == offsetof(mgsa::BatchJob, work), "mgsa_job and BatchJob must match");
 
 namespace {
 
@@ -50,6 +57,9 @@ struct DeviceGuard {
 };
 
 int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+constexpr int64_t kBatchStride = 2 * mgsa::kBatchMaxN + 8;  // doubles of partial sums per batched CTA
+constexpr int kBatchQueueWord = 16;                        // ctl[16..18]: batched job queues
 
 struct Plan {
   int grid = 1;
@@ -138,6 +148,16 @@ mgsa_status mgsa_create(mgsa_handle* h, int device) {
     mgsa_destroy(c);
     return s;
   }
+  // Batched kernels: shared memory for n <= kBatchMaxN, one CTA per SM that fits,
+  // and their per-CTA partial sums (allocated here so mgsa_qr_batched never allocates).
+  c->batch_smem = mgsa::sweep_smem_bytes(mgsa::kBatchMaxN, mgsa::kMaxChunk);
+  if ((e = mgsa::batch_prepare(device, c->batch_smem)) != cudaSuccess ||
+      (e = mgsa::batch_max_ctas(c->batch_smem, &c->batch_grid)) != cudaSuccess ||
+      (e = cudaMalloc(&c->batch_scratch, sizeof(double) * (size_t)c->batch_grid * kBatchStride)) != cudaSuccess) {
+    mgsa_status s = cuda_fail(e);
+    mgsa_destroy(c);
+    return s;
+  }
   std::memset(c->ctl_host, 0, 256);
   *h = c;
   return MGSA_OK;
@@ -149,6 +169,7 @@ mgsa_status mgsa_destroy(mgsa_handle h) {
     DeviceGuard g(h->device);
     if (h->ws) cudaFree(h->ws);
     if (h->io) cudaFree(h->io);
+    if (h->batch_scratch) cudaFree(h->batch_scratch);
     if (h->ctl) cudaFree(h->ctl);
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
   }
@@ -234,6 +255,34 @@ mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m
   cudaError_t e = cudaMemsetAsync(h->ctl, 0, sizeof(int) * mgsa::kCtlWords, cs);
   if (e != cudaSuccess) return cuda_fail(e);
   e = mgsa::sweep_launch((int)v, a, p.grid, p.smem, cs);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return MGSA_OK;
+}
+
+size_t mgsa_job_workspace_bytes(int64_t m, int n, mgsa_variant v) {
+  if (m < 1 || n < 1 || (v != MGSA_NAIVE && v != MGSA_HA && v != MGSA_HP)) return 0;
+  const int64_t cols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
+  return sizeof(double) * (size_t)round_up(m, 32) * (size_t)cols;
+}
+
+mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, int* info_dev, mgsa_stream_t s) {
+  if (!h) return fail(MGSA_ERR_INVALID, "NULL handle");
+  if (count < 0) return fail(MGSA_ERR_INVALID, "count must be >= 0");
+  if (count == 0) return MGSA_OK;
+  if (!jobs_dev || !info_dev) return fail(MGSA_ERR_INVALID, "NULL job or info array");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(MGSA_ERR_CUDA, "cannot select the device");
+  mgsa::BatchArgs ba;
+  ba.jobs = reinterpret_cast<const mgsa::BatchJob*>(jobs_dev);
+  ba.count = count;
+  ba.max_n = mgsa::kBatchMaxN;
+  ba.info = info_dev;
+  ba.queue = reinterpret_cast<unsigned int*>(h->ctl + kBatchQueueWord);
+  ba.scratch = h->batch_scratch;
+  ba.scratch_stride = kBatchStride;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+  cudaError_t e = cudaMemsetAsync(ba.queue, 0, 3 * sizeof(unsigned int), cs);
+  if (e == cudaSuccess) e = mgsa::batch_launch(ba, h->batch_grid, h->batch_smem, cs);
   if (e != cudaSuccess) return cuda_fail(e);
   return MGSA_OK;
 }

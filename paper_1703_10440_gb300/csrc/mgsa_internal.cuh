@@ -47,6 +47,36 @@ inline size_t sweep_smem_bytes(int n, int chunk) {
   return sizeof(double) * (size_t)(4 * chunk + kWarps * kmax + 2 * n + kThreads + 1 + 8);
 }
 
+// One job of the batched kernel; same layout as mgsa_job in mgsa.h.
+struct BatchJob {
+  int64_t m;
+  int32_t n;
+  int32_t variant;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const double* Z;
+  int64_t ldz;
+  double* Q;
+  int64_t ldq;
+  double* R;
+  int64_t ldr;
+  double* work;
+};
+
+constexpr int kBatchMaxN = 256;                 // largest n of a batched job
+constexpr int kBatchInfoInvalid = -2147483647;  // info of a job rejected on the device
+
+struct BatchArgs {
+  const BatchJob* jobs;
+  int count;
+  int max_n;
+  int* info;               // per job: 0, breakdown column, -column (non-finite), kBatchInfoInvalid
+  unsigned int* queue;     // next job index per variant, 3 counters (zeroed before each launch)
+  double* scratch;         // per-CTA partial sums
+  int64_t scratch_stride;  // doubles per CTA, >= 2 * max_n + 1
+};
+
 // Records the message mgsa_last_error returns on this thread (mgsa_api.cu).
 void set_last_error(const char* why);
 
@@ -54,5 +84,8 @@ void set_last_error(const char* why);
 cudaError_t sweep_prepare(int device);  // sets shared-memory attributes once per device
 cudaError_t sweep_max_ctas(int variant, size_t smem, int* max_ctas);
 cudaError_t sweep_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t batch_prepare(int device, size_t smem);
+cudaError_t batch_max_ctas(size_t smem, int* max_ctas);
+cudaError_t batch_launch(const BatchArgs& ba, int grid, size_t smem, cudaStream_t s);
 
 }  // namespace mgsa

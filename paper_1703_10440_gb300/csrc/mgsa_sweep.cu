@@ -160,6 +160,32 @@ __device__ __forceinline__ bool grid_sync(int* ctl, unsigned int& gen, int* s_fl
   return grid_wait(ctl, gen, s_flags, s_flags + 1);
 }
 
+// Synchronisation of the step body: device-wide for the single-instance
+// kernel, CTA-wide when one CTA owns a whole instance (batched kernel).
+template <bool kBatch>
+__device__ __forceinline__ void sync_arrive(int* ctl, unsigned int gen, int* s_flags) {
+  if (kBatch) __syncthreads();
+  else grid_arrive(ctl, gen, s_flags);
+}
+
+template <bool kBatch>
+__device__ __forceinline__ bool sync_wait(int* ctl, unsigned int& gen, int* s_flags) {
+  if (kBatch) {
+    __syncthreads();
+    return true;
+  }
+  return grid_wait(ctl, gen, s_flags, s_flags + 1);
+}
+
+template <bool kBatch>
+__device__ __forceinline__ bool sync_all(int* ctl, unsigned int& gen, int* s_flags) {
+  sync_arrive<kBatch>(ctl, gen, s_flags);
+  return sync_wait<kBatch>(ctl, gen, s_flags);
+}
+
+// Result of the step body: 0, or (device status << 24) | 1-based column.
+__device__ __forceinline__ int body_result(int status, int column) { return (status << 24) | (column & 0xFFFFFF); }
+
 // Sum over CTAs b (in order of b, fixed tree) of part[b * stride], by warp 0;
 // lane 0 returns the sum.
 __device__ __forceinline__ double warp0_sum_ctas(const double* part, int64_t stride, int G) {
@@ -347,11 +373,11 @@ __device__ __forceinline__ void fused_pass(int i, int n, int64_t c0, int crows, 
   __syncthreads();
 }
 
-template <int V>
-__global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs a) {
-  extern __shared__ __align__(16) double smem[];
-  __shared__ int s_wfirst[kWarps], s_wlast[kWarps];
-  __shared__ int s_flags[2];
+// The whole right-looking loop for one instance, run by G CTAs (CTA b owns
+// rows [b*rpc, (b+1)*rpc)).  Returns 0 or body_result(status, column).
+template <int V, bool kBatch>
+__device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* smem, int* s_wfirst, int* s_wlast,
+                          int* s_flags) {
   const int n = a.n;
   const int chunk = a.chunk;
   const int kmax = (n + kWarps - 1) / kWarps + 2;
@@ -362,8 +388,6 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
   double* s_buf = s_rrow + n;                // kThreads + 1 reduction scratch
   double* s_scal = s_buf + kThreads + 1;     // r_ii, 1/r_ii, status
 
-  const int G = gridDim.x;
-  const int b = blockIdx.x;
   const int tid = threadIdx.x;
   const int64_t m = a.m;
   const int64_t k0 = (int64_t)b * a.rpc;
@@ -393,28 +417,54 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
     for (int64_t t = tid; t < (int64_t)n * n; t += kThreads) R[(t % n) + (t / n) * ldr] = 0.0;
   }
   if (V == kHP) {
+    // X = A Z: four rows per thread in lockstep, kPanel columns at a time, so
+    // the gathers of four rows are in flight together.
+    constexpr int kPanel = 8;
     double s0 = 0.0;
-    for (int64_t k = k0 + tid; k < k1; k += kThreads) {
-      const int e0 = __ldg(rowptr + k), e1 = __ldg(rowptr + k + 1);
-      for (int j0 = 0; j0 < n; j0 += 8) {
-        const int w = (n - j0) < 8 ? (n - j0) : 8;
-        double acc[8];
+    for (int64_t kb = k0 + tid; kb < k1; kb += 4 * kThreads) {
+      int eb[4], ee[4];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) acc[jj] = 0.0;
-        for (int e = e0; e < e1; ++e) {
-          const double v = __ldg(val + e);
-          const double* zc = Z + __ldg(colidx + e) + (int64_t)j0 * ldz;
+      for (int q = 0; q < 4; ++q) {
+        const int64_t kk = kb + q * kThreads;
+        eb[q] = kk < k1 ? __ldg(rowptr + kk) : 0;
+        ee[q] = kk < k1 ? __ldg(rowptr + kk + 1) : 0;
+      }
+      for (int j0 = 0; j0 < n; j0 += kPanel) {
+        const int w = (n - j0) < kPanel ? (n - j0) : kPanel;
+        double acc[4][kPanel];
+        int e[4];
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj)
-            if (jj < w) acc[jj] = fma(v, __ldg(zc + jj * ldz), acc[jj]);
+        for (int q = 0; q < 4; ++q) {
+          e[q] = eb[q];
+#pragma unroll
+          for (int jj = 0; jj < kPanel; ++jj) acc[q][jj] = 0.0;
+        }
+        while (e[0] < ee[0] || e[1] < ee[1] || e[2] < ee[2] || e[3] < ee[3]) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (e[q] < ee[q]) {
+              const double v = __ldg(val + e[q]);
+              const double* zc = Z + __ldg(colidx + e[q]) + (int64_t)j0 * ldz;
+#pragma unroll
+              for (int jj = 0; jj < kPanel; ++jj)
+                if (jj < w) acc[q][jj] = fma(v, __ldg(zc + jj * ldz), acc[q][jj]);
+              ++e[q];
+            }
+          }
         }
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          if (jj < w) {
-            const double zk = __ldg(Z + k + (int64_t)(j0 + jj) * ldz);
-            X[k + (int64_t)(j0 + jj) * ldx] = acc[jj];
-            Q[k + (int64_t)(j0 + jj) * ldq] = zk;
-            if (j0 + jj == 0) s0 = fma(zk, acc[0], s0);
+        for (int q = 0; q < 4; ++q) {
+          const int64_t kk = kb + q * kThreads;
+          if (kk < k1) {
+#pragma unroll
+            for (int jj = 0; jj < kPanel; ++jj) {
+              if (jj < w) {
+                const double zk = __ldg(Z + kk + (int64_t)(j0 + jj) * ldz);
+                X[kk + (int64_t)(j0 + jj) * ldx] = acc[q][jj];
+                Q[kk + (int64_t)(j0 + jj) * ldq] = zk;
+                if (j0 + jj == 0) s0 = fma(zk, acc[q][0], s0);
+              }
+            }
           }
         }
       }
@@ -499,9 +549,9 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
         if (tid == 0) part_norm[b] = sl;
       }
       MGSA_TRACE(i, 1);
-      grid_arrive(a.ctl, gen, s_flags);
+      sync_arrive<kBatch>(a.ctl, gen, s_flags);
       if (i > 0) reduce_rest(part_prev, G, n, i - 1, s_rrow, s_buf, R, ldr, b == 0);  // r_{i-1,j}, j > i
-      if (!grid_wait(a.ctl, gen, s_flags, s_flags + 1)) return;
+      if (!sync_wait<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     } else {
       const double* zsrc;  // column i of the working Z, complete on every row
       if (i > 0) {
@@ -538,9 +588,9 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
             }
           }
         }
-        grid_arrive(a.ctl, gen, s_flags);
+        sync_arrive<kBatch>(a.ctl, gen, s_flags);
         reduce_rest(part_prev, G, n, i - 1, s_rrow, s_buf, R, ldr, b == 0);  // r_{i-1,j}, j > i
-        if (!grid_wait(a.ctl, gen, s_flags, s_flags + 1)) return;
+        if (!sync_wait<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
         zsrc = zi;
       } else {
         zsrc = Z;  // column 0 of the input equals the working column 0
@@ -587,15 +637,12 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
       sl = block_sum(sl, s_buf);
       if (tid == 0) part_norm[b] = sl;
       MGSA_TRACE(i, 1);
-      if (!grid_sync(a.ctl, gen, s_flags)) return;
+      if (!sync_all<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     }
     MGSA_TRACE(i, 2);
     diagonal(part_norm, G, s_scal);
     MGSA_TRACE(i, 3);
-    if (s_scal[2] != 0.0) {
-      if (b == 0 && tid == 0) set_status(a.ctl, (int)s_scal[2], i + 1);
-      return;  // every CTA took the same decision from the same sum
-    }
+    if (s_scal[2] != 0.0) return body_result((int)s_scal[2], i + 1);  // the same verdict in every CTA
     const double inv = s_scal[1];
     if (b == 0 && tid == 0) R[i + (int64_t)i * ldr] = s_scal[0];
 
@@ -622,7 +669,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
         }
       }
       // Other CTAs still gather z_i; q_i may overwrite it only after this wait.
-      if (!grid_sync(a.ctl, gen, s_flags)) return;
+      if (!sync_all<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     }
 
     // ---------------- fused pass ----------------
@@ -712,10 +759,81 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
     if (ncols == 0) break;
     for (int jr = tid; jr < ncols; jr += kThreads) part_cur[(int64_t)b * n + (i + 1 + jr)] = s_racc[jr];
     MGSA_TRACE(i, 7);
-    if (!grid_sync(a.ctl, gen, s_flags)) return;
+    if (!sync_all<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     MGSA_TRACE(i, 8);
     reduce_first(part_cur, G, n, i, s_rrow, R, ldr, b == 0);  // r_{i,i+1}; the rest waits for the next barrier
     MGSA_TRACE(i, 9);
+  }
+  return 0;
+}
+
+// Single instance over the whole grid (cooperative launch).
+template <int V>
+__global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs a) {
+  extern __shared__ __align__(16) double smem[];
+  __shared__ int s_wfirst[kWarps], s_wlast[kWarps];
+  __shared__ int s_flags[2];
+  const int r = sweep_body<V, false>(a, gridDim.x, blockIdx.x, smem, s_wfirst, s_wlast, s_flags);
+  // Breakdown verdicts are identical in every CTA; CTA 0 records them.  A
+  // timeout was recorded by the CTA that saw it.
+  if (r != 0 && (r >> 24) != kDevTimeout && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.ctl, r >> 24, r & 0xFFFFFF);
+}
+
+// Many independent instances: every CTA takes the next job from the queue and
+// runs the whole loop of that instance by itself (CTA-wide barriers only).
+// One launch per variant: the launch for V takes the jobs of variant V (the
+// HP launch also answers jobs whose variant is unknown).
+template <int V>
+__global__ void __launch_bounds__(kThreads, 1) mgs_batch_kernel(const BatchArgs ba) {
+  extern __shared__ __align__(16) double smem[];
+  __shared__ int s_wfirst[kWarps], s_wlast[kWarps];
+  __shared__ int s_flags[2];
+  __shared__ int s_job;
+  double* part = ba.scratch + (int64_t)blockIdx.x * ba.scratch_stride;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = (int)atomicAdd(ba.queue + V, 1u);
+    __syncthreads();
+    const int jb = s_job;
+    __syncthreads();
+    if (jb >= ba.count) break;
+    const BatchJob& J = ba.jobs[jb];
+    const int64_t m = J.m;
+    const int n = J.n;
+    const bool known = J.variant >= kNaive && J.variant <= kHP;
+    if (J.variant != V && (known || V != kHP)) continue;  // another launch's job
+    int result;
+    if (!known || n < 1 || n > ba.max_n || m < n || m >= ((int64_t)1 << 31) || J.ldz < m || J.ldq < m ||
+        J.ldr < n || !J.rowptr || !J.Z || !J.Q || !J.R || !J.work) {
+      result = -1;
+    } else {
+      SweepArgs a;
+      a.m = m;
+      a.n = n;
+      a.rowptr = J.rowptr;
+      a.col = J.col;
+      a.val = J.val;
+      a.Z = J.Z;
+      a.ldz = J.ldz;
+      a.Q = J.Q;
+      a.ldq = J.ldq;
+      a.R = J.R;
+      a.ldr = (int)J.ldr;
+      a.X = J.work;
+      a.ldx = (m + 31) / 32 * 32;
+      a.part = part;
+      a.ctl = nullptr;
+      a.rpc = (m + 31) / 32 * 32;
+      a.chunk = (int)(a.rpc < kMaxChunk ? a.rpc : kMaxChunk);
+      result = sweep_body<V, true>(a, 1, 0, smem, s_wfirst, s_wlast, s_flags);
+    }
+    if (threadIdx.x == 0) {
+      int info = 0;
+      if (result == -1) info = kBatchInfoInvalid;
+      else if ((result >> 24) == kDevBreakdown) info = result & 0xFFFFFF;
+      else if ((result >> 24) == kDevNonfinite) info = -(result & 0xFFFFFF);
+      ba.info[jb] = info;
+    }
+    __syncthreads();
   }
 }
 
@@ -750,6 +868,46 @@ cudaError_t sweep_max_ctas(int variant, size_t smem, int* max_ctas) {
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_fn(variant), kThreads, smem)) != cudaSuccess) return e;
   *max_ctas = sms * per_sm;
   return cudaSuccess;
+}
+
+static const void* batch_fn(int variant) {
+  switch (variant) {
+    case kNaive: return reinterpret_cast<const void*>(mgs_batch_kernel<kNaive>);
+    case kHA: return reinterpret_cast<const void*>(mgs_batch_kernel<kHA>);
+    default: return reinterpret_cast<const void*>(mgs_batch_kernel<kHP>);
+  }
+}
+
+cudaError_t batch_prepare(int device, size_t smem) {
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e != cudaSuccess) return e;
+  for (int v = kNaive; v <= kHP; ++v) {
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, batch_fn(v))) != cudaSuccess) return e;
+    if (smem + fa.sharedSizeBytes > (size_t)optin) return cudaErrorInvalidValue;
+    if ((e = cudaFuncSetAttribute(batch_fn(v), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t batch_max_ctas(size_t smem, int* max_ctas) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fn(kHP), kThreads, smem)) != cudaSuccess)
+    return e;
+  *max_ctas = sms * per_sm;
+  return cudaSuccess;
+}
+
+cudaError_t batch_launch(const BatchArgs& ba, int grid, size_t smem, cudaStream_t s) {
+  mgs_batch_kernel<kNaive><<<grid, kThreads, smem, s>>>(ba);
+  mgs_batch_kernel<kHA><<<grid, kThreads, smem, s>>>(ba);
+  mgs_batch_kernel<kHP><<<grid, kThreads, smem, s>>>(ba);
+  return cudaGetLastError();
 }
 
 cudaError_t sweep_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s) {

@@ -37,6 +37,17 @@ class mgsa_csr(ctypes.Structure):
                 ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
 
 
+class mgsa_job(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("Z", ctypes.c_void_p), ("ldz", ctypes.c_int64), ("Q", ctypes.c_void_p), ("ldq", ctypes.c_int64),
+                ("R", ctypes.c_void_p), ("ldr", ctypes.c_int64), ("work", ctypes.c_void_p)]
+
+
+MGSA_BATCH_MAX_N = 256
+MGSA_BATCH_INFO_INVALID = -2147483647
+
+
 class MgsaError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -59,6 +70,8 @@ SIGNATURES = {
                             ctypes.POINTER(_INT)]),
     "mgsa_set_param": (_INT, [_VP, _INT, _I64]),
     "mgsa_qr_noalloc": (_INT, [ctypes.POINTER(mgsa_csr), _VP, _I64, _INT, _I64, _INT, _VP, _I64, _VP, _INT, _VP, _VP]),
+    "mgsa_job_workspace_bytes": (_SZ, [_I64, _INT, _INT]),
+    "mgsa_qr_batched": (_INT, [_VP, _INT, _VP, _VP, _VP]),
     "mgsa_last_error": (ctypes.c_char_p, []),
 }
 MGSA_PARAM_MAX_CTAS, MGSA_PARAM_CHUNK_ROWS, MGSA_PARAM_MIN_ROWS_PER_CTA = 0, 1, 2
@@ -151,6 +164,16 @@ def mgsa_qr_noalloc(A: mgsa_csr, Z, m: int, n: int, ldz: int, variant: int, Q, l
     allocation, no handle); returns the status of the call."""
     return int(lib().mgsa_qr_noalloc(ctypes.byref(A), _ptr(Z), m, n, ldz, variant, _ptr(Q), ldq, _ptr(R), ldr,
                                      _ptr(info_dev), _stream(stream)))
+
+
+def mgsa_job_workspace_bytes(m: int, n: int, variant: int) -> int:
+    return int(lib().mgsa_job_workspace_bytes(m, n, variant))
+
+
+def mgsa_qr_batched(h: int, count: int, jobs_dev, info_dev, stream=None) -> int:
+    """Queue a batch; ``jobs_dev`` is a device buffer holding ``count``
+    ``mgsa_job`` structs, ``info_dev`` a device int32 buffer of ``count``."""
+    return int(lib().mgsa_qr_batched(h, count, _ptr(jobs_dev), _ptr(info_dev), _stream(stream)))
 
 
 def mgsa_get_info(h: int, stream=None) -> tuple[int, int]:

@@ -13,7 +13,11 @@ Default workload: 2D 5-point Laplacian on a 512 x 512 grid + 0.01 I
 each QR is timed with CUDA events on its own stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mgsa|reference]
-                    [--workload poisson2d|varcoef3d|tridiag]
+                    [--workload poisson2d|varcoef3d|tridiag|batch4096]
+
+``--workload batch4096`` measures the batched path instead: 4096 banded SPD
+instances (m ~ logU[256, 8192], n ~ U{4..64}) factored by one
+mgsa_qr_batched call per variant, against one mgsa_qr launch per instance.
 
 ``--impl reference`` times the CPU oracle (plain C, one core) on the same
 workload: each step is one QR, the variants taking turns.
@@ -353,13 +357,105 @@ def run_gpu(args, desc, A, Z, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world, local_rank):
+    """Batched path: one mgsa_qr_batched call per variant over 4096 instances."""
+    import torch
+
+    from paper_1703_10440_gb300 import mgsa
+    from paper_1703_10440_gb300.batch import Batch
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    inst = W.batch(4096)
+    # largest work first for the queue's load balance
+    order = sorted(range(len(inst)), key=lambda k: -inst[k][1].shape[0] * inst[k][1].shape[1] ** 2)
+    inst = [inst[k] for k in order]
+    batches = {v: Batch(inst, v, device=local_rank) for v in VARIANTS}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = mgsa.Handle(local_rank)
+    for _ in range(args.warmup):
+        for v in VARIANTS:
+            batches[v].run(h.h, stream)
+    torch.cuda.synchronize(dev)
+    for v in VARIANTS:
+        bad = int((batches[v].infos() != 0).sum())
+        if bad:
+            raise RuntimeError(f"{bad} batched {v} jobs failed")
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in VARIANTS]
+          for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            for vi, v in enumerate(VARIANTS):
+                flush.fill_(k & 0xFF)
+                ev[k][vi][0].record(stream)
+                batches[v].run(h.h, stream)
+                ev[k][vi][1].record(stream)
+        torch.cuda.synchronize(dev)
+    per_ms = [sum(ev[k][vi][0].elapsed_time(ev[k][vi][1]) for k in range(args.steps)) / args.steps
+              for vi in range(len(VARIANTS))]
+    # One launch per instance (the single-instance entry point), same inputs.
+    single_ms = {}
+    for v in ("hp",):
+        b = batches[v]
+        csrs = []
+        for k in range(b.count):
+            j = b.jobs_host[k]
+            csrs.append((mgsa.make_csr(int(j["m"]), 0, int(j["rowptr"]), int(j["col"]), int(j["val"])), j))
+        def per_instance():
+            for csr, j in csrs:
+                st = mgsa.mgsa_qr(h.h, csr, int(j["Z"]), int(j["m"]), int(j["n"]), int(j["ldz"]), mgsa.VARIANTS[v],
+                                  int(j["Q"]), int(j["ldq"]), int(j["R"]), int(j["ldr"]), stream)
+                if st != mgsa.MGSA_OK:
+                    raise RuntimeError(mgsa.mgsa_last_error())
+        for csr, j in csrs:
+            mgsa.mgsa_reserve(h.h, int(j["m"]), int(j["n"]), mgsa.VARIANTS[v])
+        per_instance()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        per_instance()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        single_ms[v] = e0.elapsed_time(e1)
+    h.close()
+    if rank != 0:
+        return
+    ms_sizes = [Z.shape for _, Z in inst]
+    nnz = [len(A[1]) for A, _ in inst]
+    per_variant = {}
+    for vi, v in enumerate(VARIANTS):
+        fl = sum(model(v, m, n, z)[1] for (m, n), z in zip(ms_sizes, nnz))
+        tfl = fl / per_ms[vi] / 1e9
+        per_variant[v] = {"ms": round(per_ms[vi], 3), "qr_per_s": round(len(inst) * 1e3 / per_ms[vi], 1),
+                          "model_flops": fl, "fp64_tflops": round(tfl, 4),
+                          "fp64_frac": round(tfl / FP64_PEAK_TFLOPS, 4)}
+    step_ms = sum(per_ms)
+    dom = max(VARIANTS, key=lambda v: per_variant[v]["ms"])
+    line = {"metric": METRIC, "value": 3 * len(inst) * 1e3 / step_ms, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch4096_banded_hb8_m256-8192_n4-64", "instances": len(inst),
+                       "step": "one mgsa_qr_batched call per variant (naive, ha, hp)",
+                       "l2": "flushed (256 MiB write) before every timed call"},
+            "per_variant": per_variant,
+            "roofline": {"bound": "alu", "achieved": per_variant[dom]["fp64_tflops"], "peak": round(FP64_PEAK_TFLOPS, 4),
+                         "unit": "TFLOP/s", "frac": per_variant[dom]["fp64_frac"], "traffic": None,
+                         "kernel": f"mgs_batch_kernel<{dom}>"},
+            "one_launch_per_instance": {v: {"ms": round(t, 3), "qr_per_s": round(len(inst) * 1e3 / t, 1),
+                                            "batched_speedup": round(t / per_variant[v]["ms"], 2)}
+                                        for v, t in single_ms.items()},
+            "gpu_launches": 9 * args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mgsa", choices=["mgsa", "reference"])
-    ap.add_argument("--workload", default="poisson2d", choices=["poisson2d", "varcoef3d", "tridiag"])
+    ap.add_argument("--workload", default="poisson2d", choices=["poisson2d", "varcoef3d", "tridiag", "batch4096"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -379,8 +475,11 @@ def main():
 
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    desc, A, Z = make_workload(args.workload)
-    run_gpu(args, desc, A, Z, rank, world, local_rank)
+    if args.workload == "batch4096":
+        run_batch(args, rank, world, local_rank)
+    else:
+        desc, A, Z = make_workload(args.workload)
+        run_gpu(args, desc, A, Z, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
 

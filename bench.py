@@ -19,6 +19,10 @@ each QR is timed with CUDA events on its own stream.
 instances (m ~ logU[256, 8192], n ~ U{4..64}) factored by one
 mgsa_qr_batched call per variant, against one mgsa_qr launch per instance.
 
+``--workload served`` runs the continuous-batching server on a Poisson stream
+of requests (default 2000/s for 30 s; --serve-rate / --serve-seconds change
+it and are reported in the line) and reports p50 / p99 latency and QRs/s.
+
 ``--impl reference`` times the CPU oracle (plain C, one core) on the same
 workload: each step is one QR, the variants taking turns.
 """
@@ -449,13 +453,57 @@ def run_batch(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_served(args, rank, world, local_rank):
+    """Served stream: Poisson arrivals (default 2000/s for 30 s), m ~ logU[1e3, 1e6],
+    n ~ U{8..128}, 50/50 Laplacian / banded, 120 GB admission budget."""
+    import torch
+
+    from paper_1703_10440_gb300 import mgsa
+    from paper_1703_10440_gb300.serve import Request, Server, poisson_arrivals
+
+    torch.cuda.set_device(local_rank)
+    reqs = poisson_arrivals(args.serve_rate, args.serve_seconds, seed=W.SEED + rank)
+    h = mgsa.Handle(local_rank)
+    srv = Server(h.h, args.serve_variant, budget_bytes=120e9, small_work=args.serve_small_work, device=local_rank)
+    # warm-up: a few requests alone
+    srv.run([Request(10**7 + k, r.m, r.n, r.kind, 0.0, r.seed) for k, r in enumerate(reqs[:4])], realtime=False)
+    with ClockSampler(local_rank) as clk:
+        stats = srv.run(reqs, realtime=True)
+    # solo latency of a sample: each request served alone on an idle GPU
+    g = np.random.Generator(np.random.PCG64(7))
+    sample = [reqs[k] for k in sorted(g.choice(len(reqs), size=min(40, len(reqs)), replace=False))]
+    solo = []
+    for r in sample:
+        one = Request(r.rid, r.m, r.n, r.kind, 0.0, r.seed)
+        st = srv.run([one], realtime=False)
+        solo.append(st["p50_ms"])
+    h.close()
+    if rank != 0:
+        return
+    solo_med = float(np.median(solo))
+    line = {"metric": METRIC, "value": stats["qr_per_s"] * world, "unit": UNIT, "n_gpus": world, "steps": 1,
+            "warmup": 1, "ms_per_step": stats["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "served_poisson_m1e3-1e6_n8-128_laplace/banded", "rate_per_s": args.serve_rate,
+                       "seconds": args.serve_seconds, "requests": stats["requests"], "variant": args.serve_variant,
+                       "budget_gb": 120, "small_work": args.serve_small_work},
+            "served": {**stats, "solo_p50_ms_sample": solo_med, "p99_over_solo": stats["p99_ms"] / solo_med},
+            "gpu_launches": stats["launches"], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mgsa", choices=["mgsa", "reference"])
-    ap.add_argument("--workload", default="poisson2d", choices=["poisson2d", "varcoef3d", "tridiag", "batch4096"])
+    ap.add_argument("--workload", default="poisson2d",
+                    choices=["poisson2d", "varcoef3d", "tridiag", "batch4096", "served"])
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="served: arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="served: arrival window")
+    ap.add_argument("--serve-variant", default="hp", choices=["naive", "ha", "hp"])
+    ap.add_argument("--serve-small-work", type=float, default=2e7, help="served: m*n^2 up to which the batched kernel runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -477,6 +525,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     if args.workload == "batch4096":
         run_batch(args, rank, world, local_rank)
+    elif args.workload == "served":
+        run_served(args, rank, world, local_rank)
     else:
         desc, A, Z = make_workload(args.workload)
         run_gpu(args, desc, A, Z, rank, world, local_rank)

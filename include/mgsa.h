@@ -128,6 +128,14 @@ mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m
  * failure. */
 mgsa_status mgsa_get_info(mgsa_handle h, mgsa_stream_t s, int* info);
 
+/* Stream-ordered copy of the outcome of the last mgsa_qr queued on h into
+ * device memory: info_dev[0] = 0 (success), 2 (breakdown), 3 (non-finite) or
+ * 6 (timeout); info_dev[1] = the 1-based column (-1 for a timeout).  Queue it
+ * on the same stream right after mgsa_qr to keep the status of that QR when
+ * more QRs follow on the handle (mgsa_get_info only sees the latest one).
+ * Does not wait. */
+mgsa_status mgsa_copy_info(mgsa_handle h, int* info_dev, mgsa_stream_t s);
+
 /* End-to-end call on HOST buffers (pageable or pinned): copies the CSR arrays
  * and Z to device buffers owned by the handle, runs mgsa_qr, copies Q and R
  * back, waits for stream s and returns the outcome as mgsa_get_info would

@@ -287,6 +287,15 @@ mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, 
   return MGSA_OK;
 }
 
+mgsa_status mgsa_copy_info(mgsa_handle h, int* info_dev, mgsa_stream_t s) {
+  if (!h || !info_dev) return fail(MGSA_ERR_INVALID, "NULL handle or info_dev");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(MGSA_ERR_CUDA, "cannot select the device");
+  cudaError_t e = cudaMemcpyAsync(info_dev, h->ctl, 2 * sizeof(int), cudaMemcpyDeviceToDevice,
+                                  reinterpret_cast<cudaStream_t>(s));
+  return e == cudaSuccess ? MGSA_OK : cuda_fail(e);
+}
+
 mgsa_status mgsa_get_info(mgsa_handle h, mgsa_stream_t s, int* info) {
   if (!h || !info) return fail(MGSA_ERR_INVALID, "NULL handle or info");
   DeviceGuard g(h->device);

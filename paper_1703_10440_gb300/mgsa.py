@@ -66,6 +66,7 @@ SIGNATURES = {
     "mgsa_workspace_bytes": (_SZ, [_VP, _I64, _INT, _INT]),
     "mgsa_qr": (_INT, [_VP, ctypes.POINTER(mgsa_csr), _VP, _I64, _INT, _I64, _INT, _VP, _I64, _VP, _INT, _VP]),
     "mgsa_get_info": (_INT, [_VP, _VP, ctypes.POINTER(_INT)]),
+    "mgsa_copy_info": (_INT, [_VP, _VP, _VP]),
     "mgsa_qr_host": (_INT, [_VP, _VP, _VP, _VP, _I64, _VP, _I64, _INT, _I64, _INT, _VP, _I64, _VP, _INT, _VP,
                             ctypes.POINTER(_INT)]),
     "mgsa_set_param": (_INT, [_VP, _INT, _I64]),
@@ -174,6 +175,10 @@ def mgsa_qr_batched(h: int, count: int, jobs_dev, info_dev, stream=None) -> int:
     """Queue a batch; ``jobs_dev`` is a device buffer holding ``count``
     ``mgsa_job`` structs, ``info_dev`` a device int32 buffer of ``count``."""
     return int(lib().mgsa_qr_batched(h, count, _ptr(jobs_dev), _ptr(info_dev), _stream(stream)))
+
+
+def mgsa_copy_info(h: int, info_dev, stream=None) -> None:
+    _check(lib().mgsa_copy_info(h, _ptr(info_dev), _stream(stream)))
 
 
 def mgsa_get_info(h: int, stream=None) -> tuple[int, int]:

@@ -1,0 +1,236 @@
+"""Continuous-batching server for A-orthonormal QR requests.
+
+The client of this loop is a projection eigensolver or a block-GMRES code
+that asks for many A-orthonormalisations of different sizes.  The server:
+
+* admits arrived requests in arrival order while the device-memory budget
+  allows (A, Z, Q, R and, for batched requests, the x/p workspace stay
+  resident on the device until the request completes);
+* every tick, puts all admitted small requests (m * n^2 <= ``small_work``)
+  into ONE ``mgsa_qr_batched`` call -- a persistent kernel in which every CTA
+  runs one instance, so requests of different sizes run side by side -- and
+  gives each large request its own ``mgsa_qr`` launch over the whole GPU;
+* keeps ticking while earlier launches run (continuous batching): requests
+  that arrive meanwhile are admitted as memory frees up and launched behind
+  the work in flight;
+* timestamps completion with CUDA events and reports per-request latency
+  (arrival to device completion) as p50 / p99 beside throughput.
+
+Inputs are drawn on the device at admission (``workloads.device``) on a side
+stream; the QR stream waits for them with an event.  Scheduling is host
+Python; every step of the QRs runs in libmgsa's kernels.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+from . import mgsa
+from .batch import JOB_DTYPE, _round
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    m: int
+    n: int
+    kind: str            # 'laplace' | 'banded'
+    arrival: float       # seconds after the start of the run
+    seed: int = 20170330
+    # filled in by the server
+    A: tuple | None = None
+    Z: object = None
+    Q: object = None
+    R: object = None
+    work: object = None
+    nbytes: int = 0
+    small: bool = False
+    t_done: float = math.nan
+    info: int = -99
+    info_buf: object = None
+
+
+def poisson_arrivals(rate: float, duration: float, seed: int = 20170330, m_lo: float = 1e3, m_hi: float = 1e6,
+                     n_lo: int = 8, n_hi: int = 128) -> list[Request]:
+    """Arrivals of a Poisson process of ``rate`` per second over ``duration``
+    seconds; m ~ logU[m_lo, m_hi], n ~ U{n_lo..n_hi}, matrix kind 50/50."""
+    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 50])))
+    t, out = 0.0, []
+    while True:
+        t += g.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        m = int(round(math.exp(g.uniform(math.log(m_lo), math.log(m_hi)))))
+        n = int(g.integers(n_lo, n_hi + 1))
+        kind = "laplace" if g.random() < 0.5 else "banded"
+        out.append(Request(len(out), m, n, kind, t, seed))
+    return out
+
+
+class Server:
+    def __init__(self, handle: int, variant: str = "hp", budget_bytes: float = 120e9, small_work: float = 2e7,
+                 device: int = 0, max_batch: int = 4096, max_m: int = 1_000_000, max_n: int = 128):
+        import torch
+
+        self.torch = torch
+        self.h = handle
+        self.variant = variant
+        self.v = mgsa.VARIANTS[variant]
+        self.budget = budget_bytes
+        self.small_work = small_work
+        self.dev = torch.device("cuda", device)
+        self.max_batch = max_batch
+        self.stream = torch.cuda.Stream(self.dev)
+        self.gen_stream = torch.cuda.Stream(self.dev)
+        # Large requests share the handle's workspace: size it once, up front.
+        mgsa.mgsa_reserve(handle, max_m, max_n, self.v)
+        self.shared_ws = mgsa.mgsa_workspace_bytes(handle, max_m, max_n, self.v)
+
+    # -- admission ---------------------------------------------------------
+    def _bytes(self, r: Request) -> int:
+        m, n = r.m, r.n
+        nnz = 5 * m if r.kind == "laplace" else 17 * m
+        b = 12 * nnz + 4 * (m + 1) + 2 * 8 * m * n + 8 * n * n
+        if r.m * r.n ** 2 <= self.small_work:
+            b += mgsa.mgsa_job_workspace_bytes(m, n, self.v)
+        return b
+
+    def _materialize(self, r: Request):
+        from workloads import device as wd
+
+        torch = self.torch
+        with torch.cuda.stream(self.gen_stream):
+            r.A, r.Z, r.m = wd.request_inputs(r.kind, r.m, r.n, r.seed, r.rid, self.dev)
+            r.n = r.Z.shape[1]
+            r.Q = torch.empty((r.n, _round(r.m)), dtype=torch.float64, device=self.dev)
+            r.R = torch.empty((r.n, r.n), dtype=torch.float64, device=self.dev)
+            r.small = r.m * r.n ** 2 <= self.small_work
+            if r.small:
+                r.work = torch.empty(mgsa.mgsa_job_workspace_bytes(r.m, r.n, self.v) // 8 + 1, dtype=torch.float64,
+                                     device=self.dev)
+            r.info_buf = torch.zeros(2, dtype=torch.int32, device=self.dev)
+
+    def _release(self, r: Request):
+        r.A = r.Z = r.Q = r.R = r.work = r.info_buf = None
+
+    # -- launches ----------------------------------------------------------
+    def _launch(self, admitted: list[Request], ref_event):
+        torch = self.torch
+        ready = torch.cuda.Event()
+        ready.record(self.gen_stream)
+        self.stream.wait_event(ready)
+        groups = []
+        small = [r for r in admitted if r.small]
+        large = [r for r in admitted if not r.small]
+        if small:
+            small.sort(key=lambda r: -r.m * r.n ** 2)
+            jobs = np.zeros(len(small), dtype=JOB_DTYPE)
+            for k, r in enumerate(small):
+                rowptr, col, val = r.A
+                jobs[k] = (r.m, r.n, self.v, rowptr.data_ptr(), col.data_ptr(), val.data_ptr(), r.Z.data_ptr(), r.m,
+                           r.Q.data_ptr(), r.Q.stride(0), r.R.data_ptr(), r.n, r.work.data_ptr())
+            # pinned + non_blocking: the host loop must not wait behind the work in flight
+            jobs_host = torch.from_numpy(jobs.view(np.uint8).copy()).pin_memory()
+            with torch.cuda.stream(self.stream):
+                jobs_dev = jobs_host.to(self.dev, non_blocking=True)
+                info = torch.zeros(len(small), dtype=torch.int32, device=self.dev)
+            st = mgsa.mgsa_qr_batched(self.h, len(small), jobs_dev, info, self.stream)
+            if st != mgsa.MGSA_OK:
+                raise mgsa.MgsaError(st, mgsa.mgsa_last_error())
+            done = torch.cuda.Event(enable_timing=True)
+            done.record(self.stream)
+            groups.append(("batch", small, done, (jobs_dev, info, jobs_host)))
+        for r in large:
+            rowptr, col, val = r.A
+            csr = mgsa.make_csr(r.m, col.numel(), rowptr, col, val)
+            st = mgsa.mgsa_qr(self.h, csr, r.Z, r.m, r.n, r.m, self.v, r.Q, r.Q.stride(0), r.R, r.n, self.stream)
+            if st != mgsa.MGSA_OK:
+                raise mgsa.MgsaError(st, mgsa.mgsa_last_error())
+            mgsa.mgsa_copy_info(self.h, r.info_buf, self.stream)
+            done = torch.cuda.Event(enable_timing=True)
+            done.record(self.stream)
+            groups.append(("single", [r], done, None))
+        return groups
+
+    # -- the loop ----------------------------------------------------------
+    def run(self, requests: list[Request], realtime: bool = True) -> dict:
+        """Serve ``requests`` (arrival times relative to the start).  With
+        ``realtime`` False every request is considered arrived at t = 0."""
+        torch = self.torch
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting: collections.deque = collections.deque()
+        inflight: collections.deque = collections.deque()
+        used = self.shared_ws
+        peak = used
+        torch.cuda.synchronize(self.dev)
+        ref = torch.cuda.Event(enable_timing=True)
+        ref.record(self.stream)
+        ref.synchronize()
+        t0 = time.perf_counter()
+        ticks = launches = 0
+        while pending or waiting or inflight:
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0].arrival <= now):
+                waiting.append(pending.popleft())
+            admitted = []
+            while waiting and len(admitted) < self.max_batch:
+                need = self._bytes(waiting[0])
+                if used + need > self.budget and (inflight or admitted):
+                    break
+                r = waiting.popleft()
+                self._materialize(r)
+                r.nbytes = need
+                used += need
+                admitted.append(r)
+            peak = max(peak, used)
+            if admitted:
+                for g in self._launch(admitted, ref):
+                    inflight.append(g)
+                    launches += 1
+                ticks += 1
+            progressed = bool(admitted)
+            while inflight and inflight[0][2].query():
+                kind, reqs, done, extra = inflight.popleft()
+                t_done = ref.elapsed_time(done) / 1e3
+                if kind == "batch":
+                    infos = extra[1].cpu().numpy()
+                else:
+                    infos = [int(reqs[0].info_buf[0].item())]
+                for r, inf in zip(reqs, infos):
+                    r.t_done = t_done
+                    r.info = int(inf)
+                    used -= r.nbytes
+                progressed = True
+                for r in reqs:
+                    self._keep(r)
+            if not progressed:
+                time.sleep(50e-6)
+        torch.cuda.synchronize(self.dev)
+        lat = np.array([r.t_done - r.arrival for r in requests])
+        first = min(r.arrival for r in requests)
+        last = max(r.t_done for r in requests)
+        return {"requests": len(requests), "ok": int(sum(r.info == 0 for r in requests)),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "qr_per_s": len(requests) / (last - first),
+                "makespan_s": last - first, "ticks": ticks, "launches": launches, "peak_bytes": peak,
+                "small": int(sum(r.small for r in requests))}
+
+    # Results are dropped after completion unless a subclass keeps them.
+    def _keep(self, r: Request):
+        self._release(r)
+
+
+class KeepingServer(Server):
+    """Keeps Q and R of every request on the host (for tests)."""
+
+    def __init__(self, *a, **kw):
+        super().__init__(*a, **kw)
+        self.results = {}
+
+    def _keep(self, r: Request):
+        self.results[r.rid] = (r.Q[:, : r.m].T.cpu().numpy(), r.R.T.cpu().numpy(), r.info)
+        self._release(r)

@@ -1,0 +1,74 @@
+"""The continuous-batching server: every request's result is the same when it
+is served alone and when it is served in a mix of concurrent requests of
+different sizes (batched and whole-GPU launches interleaved), and agrees with
+the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1703_10440_gb300 import mgsa  # noqa: E402
+from paper_1703_10440_gb300.serve import KeepingServer, Request, poisson_arrivals  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def handle():
+    h = mgsa.Handle(0)
+    yield h
+    h.close()
+
+
+def make_requests():
+    reqs = poisson_arrivals(rate=400.0, duration=0.1, m_lo=1e3, m_hi=6e4, n_lo=8, n_hi=48)
+    assert len(reqs) >= 20
+    return reqs
+
+
+def fresh(reqs):
+    return [Request(r.rid, r.m, r.n, r.kind, r.arrival, r.seed) for r in reqs]
+
+
+def test_served_alone_equals_in_mix(handle):
+    reqs = make_requests()
+    # small_work splits the mix between the batched kernel and whole-GPU launches
+    mix = KeepingServer(handle.h, "hp", budget_bytes=8e9, small_work=5e6, max_m=60000, max_n=48)
+    stats = mix.run(fresh(reqs), realtime=True)
+    assert stats["ok"] == len(reqs)
+    assert 0 < stats["small"] < len(reqs)
+    alone = KeepingServer(handle.h, "hp", budget_bytes=8e9, small_work=5e6, max_m=60000, max_n=48)
+    for r in fresh(reqs):
+        alone.run([Request(r.rid, r.m, r.n, r.kind, 0.0, r.seed)], realtime=False)
+    for rid, (Q, R, info) in mix.results.items():
+        Qa, Ra, info_a = alone.results[rid]
+        assert info == info_a == 0
+        assert np.linalg.norm(R - Ra) / np.linalg.norm(Ra) <= 1e-12
+        assert np.abs(Q - Qa).max() <= 1e-10 * np.abs(Qa).max()
+
+
+def test_served_results_match_oracle(handle):
+    from workloads import device as wd
+
+    reqs = fresh(make_requests())[:6]
+    srv = KeepingServer(handle.h, "ha", budget_bytes=8e9, small_work=5e6, max_m=60000, max_n=48)
+    srv.run(reqs, realtime=False)
+    for r in reqs:
+        A, Z, m = wd.request_inputs(r.kind, r.m, r.n, r.seed, r.rid, torch.device("cuda"))
+        A = tuple(t.cpu().numpy() for t in A)
+        Z = np.asfortranarray(Z.cpu().numpy())
+        Q, R, info = srv.results[r.rid]
+        Qo, Ro, oinfo, _, _ = oracle.mgs(A, Z, "ha", "row")
+        assert info == 0 and oinfo == 0
+        assert oracle.repr_error(Z, Q, R) <= max(1e-13, 10 * oracle.repr_error(Z, Qo, Ro))
+        assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 1e-10
+
+
+def test_admission_under_a_tight_budget(handle):
+    reqs = fresh(make_requests())[:10]
+    srv = KeepingServer(handle.h, "hp", budget_bytes=2.5e8, small_work=5e6, max_m=60000, max_n=48)
+    stats = srv.run(reqs, realtime=False)
+    assert stats["ok"] == len(reqs)
+    biggest = max(srv._bytes(r) for r in reqs)
+    assert stats["peak_bytes"] <= 2.5e8 + biggest

@@ -44,6 +44,17 @@
  */
 #include <math.h>
 #include <stdint.h>
+
+/* ORACLE_MUTANT (test builds only) plants one known mistake so that the test
+ * suite can show its pins catch it:
+ *   1  MGS-HA forms p_j = A q_j with a second MV (i.e. it becomes naive)
+ *   2  MGS-HP leaves x_j = A z_j^{(0)} (drops eq. (tec2)'s recurrence)
+ *   3  the rank-1 update adds instead of subtracting
+ *   4  r_ij uses the Euclidean inner product q_i^T z_j instead of p_i^T z_j
+ * The default build (ORACLE_MUTANT undefined or 0) has none of them. */
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -72,7 +83,11 @@ static double dot(int64_t m, const double* a, const double* b) {
 
 /* y = y - alpha * x  (the AXPY of eq. (AXPY)). */
 static void axpy_sub(int64_t m, double alpha, const double* x, double* y) {
+#if ORACLE_MUTANT == 3
+  for (int64_t k = 0; k < m; ++k) y[k] = y[k] + alpha * x[k];
+#else
   for (int64_t k = 0; k < m; ++k) y[k] = y[k] - alpha * x[k];
+#endif
 }
 
 /* y = x / alpha  (the scaling of eq. (scaling)). */
@@ -158,7 +173,11 @@ int oracle_mgs_naive_row(int64_t m, int n, const int32_t* rowptr, const int32_t*
     csr_mv(m, rowptr, col, val, zi, p); /* p_i = A q_i */
     ++*mv_count;
     for (int j = i + 1; j < n; ++j) {
+#if ORACLE_MUTANT == 4
+      RR(i, j) = dot(m, zi, QC(j));
+#else
       RR(i, j) = dot(m, p, QC(j));   /* r_ij = p_i^T z_j^{(i-1)} */
+#endif
       axpy_sub(m, RR(i, j), zi, QC(j)); /* z_j^{(i)} */
     }
   }
@@ -220,9 +239,17 @@ int oracle_mgs_ha_row(int64_t m, int n, const int32_t* rowptr, const int32_t* co
     if (!diag_ok(s, kind)) { info = i + 1; break; }
     RR(i, i) = sqrt(s);
     scale_div(m, zi, RR(i, i), zi); /* q_i */
+#if ORACLE_MUTANT == 1
+    csr_mv(m, rowptr, col, val, zi, p);
+#else
     scale_div(m, x, RR(i, i), p);   /* p_i = x_i / r_ii */
+#endif
     for (int j = i + 1; j < n; ++j) {
+#if ORACLE_MUTANT == 4
+      RR(i, j) = dot(m, zi, QC(j));
+#else
       RR(i, j) = dot(m, p, QC(j));
+#endif
       axpy_sub(m, RR(i, j), zi, QC(j));
     }
   }
@@ -290,10 +317,16 @@ int oracle_mgs_hp_row(int64_t m, int n, const int32_t* rowptr, const int32_t* co
     scale_div(m, zi, RR(i, i), zi); /* q_i */
     scale_div(m, xi, RR(i, i), xi); /* p_i */
     for (int j = i + 1; j < n; ++j) {
+#if ORACLE_MUTANT == 4
+      RR(i, j) = dot(m, zi, QC(j));
+#else
       RR(i, j) = dot(m, xi, QC(j));
+#endif
       axpy_sub(m, RR(i, j), zi, QC(j));
     }
+#if ORACLE_MUTANT != 2
     for (int j = i + 1; j < n; ++j) axpy_sub(m, RR(i, j), xi, X + (int64_t)j * m); /* x_j^{(i)} */
+#endif
   }
   free(X);
   return info;

@@ -71,6 +71,9 @@ def make_workload(name: str):
     elif name == "tridiag":
         A, Z = W.tridiag()
         desc = "tridiag_m4096_n16"
+    elif name == "denseband":
+        A, Z = W.denseband()
+        desc = "denseband_m9180_hb194_n50_nnz3.5e6"
     else:
         raise SystemExit(f"unknown workload {name}")
     return desc, A, Z
@@ -499,7 +502,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mgsa", choices=["mgsa", "reference"])
     ap.add_argument("--workload", default="poisson2d",
-                    choices=["poisson2d", "varcoef3d", "tridiag", "batch4096", "served"])
+                    choices=["poisson2d", "varcoef3d", "tridiag", "denseband", "batch4096", "served"])
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="served: arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="served: arrival window")
     ap.add_argument("--serve-variant", default="hp", choices=["naive", "ha", "hp"])

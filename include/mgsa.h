@@ -200,7 +200,8 @@ mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, 
  *                                SM that fits, i.e. the co-resident maximum)
  *   MGSA_PARAM_CHUNK_ROWS        rows whose pivot vectors are staged in shared
  *                                memory at once (multiple of 32, <= 4096)
- *   MGSA_PARAM_MIN_ROWS_PER_CTA  smallest row slab given to one CTA (default 128)
+ *   MGSA_PARAM_MIN_ROWS_PER_CTA  smallest row slab given to one CTA (default 128,
+ *                                or 32 when A averages >= 32 nonzeros per row)
  * Results stay deterministic for a fixed setting; different settings change the
  * reduction tree and therefore the last bits of Q and R.  Returns
  * MGSA_ERR_INVALID for an unknown parameter or an out-of-range value. */

@@ -72,9 +72,12 @@ struct Plan {
   size_t part_bytes = 0;
 };
 
-mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, Plan* p) {
+// nnz < 0: unknown (workspace sizing); long rows (warp-per-row MVs) carry
+// more work per row, so they get smaller slabs and thus more CTAs.
+mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, Plan* p, int64_t nnz = -1) {
   const int chunk_cap = h->chunk_rows > 0 ? h->chunk_rows : mgsa::kMaxChunk;
-  const int64_t min_rows = h->min_rows > 0 ? h->min_rows : mgsa::kMinRowsPerCta;
+  const bool long_rows = nnz >= (int64_t)mgsa::kWarpRowNnz * m;
+  const int64_t min_rows = h->min_rows > 0 ? h->min_rows : (long_rows ? mgsa::kMinRowsLongRows : mgsa::kMinRowsPerCta);
   int max_ctas = 0;
   cudaError_t e = mgsa::sweep_max_ctas((int)v, mgsa::sweep_smem_bytes(n, chunk_cap), &max_ctas);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -89,7 +92,8 @@ mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, P
   p->ldx = round_up(m, 32);
   p->xcols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
   p->x_bytes = (size_t)round_up((int64_t)sizeof(double) * p->ldx * p->xcols, 256);
-  p->part_bytes = sizeof(double) * (size_t)(2 * n + 1) * (size_t)p->grid;
+  // Partials for the largest grid any plan can use, so a reservation fits every nnz.
+  p->part_bytes = sizeof(double) * (size_t)(2 * n + 1) * (size_t)std::max<int64_t>(max_ctas, p->grid);
   return MGSA_OK;
 }
 
@@ -229,7 +233,7 @@ mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m
   DeviceGuard g(h->device);
   if (!g.ok) return fail(MGSA_ERR_CUDA, "cannot select the device");
   Plan p;
-  if ((st = make_plan(h, m, n, v, &p)) != MGSA_OK) return st;
+  if ((st = make_plan(h, m, n, v, &p, A->nnz)) != MGSA_OK) return st;
   if ((st = ensure_ws(h, p.x_bytes + p.part_bytes)) != MGSA_OK) return st;
 
   mgsa::SweepArgs a;
@@ -250,6 +254,7 @@ mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m
   a.ctl = h->ctl;
   a.rpc = p.rpc;
   a.chunk = p.chunk;
+  a.mv_warp = A->nnz >= (int64_t)mgsa::kWarpRowNnz * m;
 
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
   cudaError_t e = cudaMemsetAsync(h->ctl, 0, sizeof(int) * mgsa::kCtlWords, cs);

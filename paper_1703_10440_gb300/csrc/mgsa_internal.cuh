@@ -10,6 +10,7 @@ constexpr int kThreads = 512;             // threads per CTA of the single-insta
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxChunk = 4096;           // rows whose pivots are staged in shared memory at once
 constexpr int kMinRowsPerCta = 128;       // smallest row slab worth a CTA
+constexpr int kMinRowsLongRows = 32;      // the same when rows are long (warp-per-row MVs)
 constexpr unsigned long long kSpinLimitNs = 4000000000ull;  // 4 s bound on any device-wide wait
 
 // Control block layout (int32 words, device memory, zeroed before each launch).
@@ -39,7 +40,11 @@ struct SweepArgs {
   int* ctl;        // control block (CtlWord)
   int64_t rpc;     // rows per CTA, multiple of 32
   int chunk;       // rows per staged chunk, multiple of 32
+  int mv_warp;     // 1: one warp per CSR row in the MVs / block product (long rows)
 };
+
+// Average row length from which a warp, not a thread, takes one CSR row.
+constexpr int kWarpRowNnz = 32;
 
 // Shared memory bytes the single-instance kernel needs for n columns and a chunk.
 inline size_t sweep_smem_bytes(int n, int chunk) {

@@ -91,12 +91,15 @@ extern "C" mgsa_status mgsa_qr_noalloc(const mgsa_csr* A, const double* Z, int64
   if (st != MGSA_OK) return st;
 
   // Launch shape: the defaults of mgsa_qr (one CTA per SM that fits, slabs of
-  // at least kMinRowsPerCta rows, pivot chunks of kMaxChunk rows).
+  // at least kMinRowsPerCta rows -- kMinRowsLongRows for long rows -- and
+  // pivot chunks of kMaxChunk rows).
   int max_ctas = 0;
   if ((e = mgsa::sweep_max_ctas((int)v, mgsa::sweep_smem_bytes(n, mgsa::kMaxChunk), &max_ctas)) != cudaSuccess)
     return cuda_fail(e);
   if (max_ctas < 1) return fail(MGSA_ERR_CUDA, "sweep kernel does not fit on this device");
-  int64_t g = std::min<int64_t>(max_ctas, (m + mgsa::kMinRowsPerCta - 1) / mgsa::kMinRowsPerCta);
+  const int64_t min_rows =
+      A->nnz >= (int64_t)mgsa::kWarpRowNnz * m ? mgsa::kMinRowsLongRows : mgsa::kMinRowsPerCta;
+  int64_t g = std::min<int64_t>(max_ctas, (m + min_rows - 1) / min_rows);
   g = std::max<int64_t>(g, 1);
   const int64_t rpc = round_up((m + g - 1) / g, 32);
   const int grid = (int)((m + rpc - 1) / rpc);
@@ -129,6 +132,7 @@ extern "C" mgsa_status mgsa_qr_noalloc(const mgsa_csr* A, const double* Z, int64
   a.ldx = ldx;
   a.rpc = rpc;
   a.chunk = chunk;
+  a.mv_warp = A->nnz >= (int64_t)mgsa::kWarpRowNnz * m;
 
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
   // The status and barrier words must start at zero; the rest of the array is

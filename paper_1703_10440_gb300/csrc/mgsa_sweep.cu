@@ -298,6 +298,29 @@ __device__ __forceinline__ void csr_rows4(const int32_t* __restrict__ rowptr, co
   }
 }
 
+// Long rows: one warp per row.  Lane l takes the entries e0 + l, e0 + l + 32,
+// ... (coalesced column and value loads), two accumulators, then a butterfly;
+// every lane returns the row's sum (a fixed tree, so deterministic).
+__device__ __forceinline__ double csr_row_warp(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                               const double* __restrict__ val, const double* src, double scale,
+                                               bool scale_src, int64_t k) {
+  const int lane = threadIdx.x & 31;
+  const int e0 = __ldg(rowptr + k), e1 = __ldg(rowptr + k + 1);
+  double acc0 = 0.0, acc1 = 0.0;
+  int e = e0 + lane;
+  for (; e + 32 < e1; e += 64) {
+    const double g0 = ld_cg(src + __ldg(colidx + e));
+    const double g1 = ld_cg(src + __ldg(colidx + e + 32));
+    acc0 = fma(__ldg(val + e), scale_src ? g0 * scale : g0, acc0);
+    acc1 = fma(__ldg(val + e + 32), scale_src ? g1 * scale : g1, acc1);
+  }
+  if (e < e1) {
+    const double g0 = ld_cg(src + __ldg(colidx + e));
+    acc0 = fma(__ldg(val + e), scale_src ? g0 * scale : g0, acc0);
+  }
+  return warp_sum(acc0 + acc1);
+}
+
 // The fused pass over one chunk of rows [c0, c0 + crows) and the columns
 // j = i+1 .. n-1: apply step i-1's updates z_j -= r_{i-1,j} q_{i-1} (HP:
 // x_j -= r_{i-1,j} p_{i-1}) and accumulate p_i^T z_j.  Work units are
@@ -416,7 +439,45 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
   if (b == 0) {
     for (int64_t t = tid; t < (int64_t)n * n; t += kThreads) R[(t % n) + (t / n) * ldr] = 0.0;
   }
-  if (V == kHP) {
+  if (V == kHP && a.mv_warp) {
+    // X = A Z with one warp per (long) row, kPanel columns at a time: lanes
+    // split the row's entries, one butterfly per column.
+    constexpr int kPanel = 8;
+    const int lane = tid & 31, warp = tid >> 5;
+    double s0 = 0.0;
+    for (int64_t k = k0 + warp; k < k1; k += kWarps) {
+      const int e0 = __ldg(rowptr + k), e1 = __ldg(rowptr + k + 1);
+      for (int j0 = 0; j0 < n; j0 += kPanel) {
+        const int w = (n - j0) < kPanel ? (n - j0) : kPanel;
+        double acc[kPanel];
+#pragma unroll
+        for (int jj = 0; jj < kPanel; ++jj) acc[jj] = 0.0;
+        for (int e = e0 + lane; e < e1; e += 32) {
+          const double v = __ldg(val + e);
+          const double* zc = Z + __ldg(colidx + e) + (int64_t)j0 * ldz;
+#pragma unroll
+          for (int jj = 0; jj < kPanel; ++jj)
+            if (jj < w) acc[jj] = fma(v, __ldg(zc + jj * ldz), acc[jj]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < kPanel; ++jj) {
+          if (jj < w) {
+            const double x = warp_sum(acc[jj]);
+            if (lane == jj) {
+              const double zk = __ldg(Z + k + (int64_t)(j0 + jj) * ldz);
+              X[k + (int64_t)(j0 + jj) * ldx] = x;
+              Q[k + (int64_t)(j0 + jj) * ldq] = zk;
+              if (j0 + jj == 0) s0 = fma(zk, x, s0);
+            }
+          }
+        }
+      }
+    }
+    if (!resident) {
+      s0 = block_sum(s0, s_buf);
+      if (tid == 0) part_norm[b] = s0;
+    }
+  } else if (V == kHP) {
     // X = A Z: four rows per thread in lockstep, kPanel columns at a time, so
     // the gathers of four rows are in flight together.
     constexpr int kPanel = 8;
@@ -604,7 +665,33 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       }
       // x_i = A z_i^{(i-1)}  (Algorithm 4/7: the per-column MV)
       double sl = 0.0;
-      if (resident) {
+      if (a.mv_warp) {
+        // One warp per row.  Resident mode: the row sums pass through this
+        // step's p slot of the pivot buffer (free until the pivots are
+        // formed) to the threads that own the rows.
+        const int lane = tid & 31, warp = tid >> 5;
+        double* xtmp = s_piv + (2 * cur + 1) * chunk;
+        for (int64_t k = k0 + warp; k < k1; k += kWarps) {
+          const double x = csr_row_warp(rowptr, colidx, val, zsrc, 1.0, false, k);
+          if (lane == 0) {
+            if (resident) {
+              xtmp[k - k0] = x;
+            } else {
+              X[k] = x;
+              sl = fma(ld_cg(zsrc + k), x, sl);
+            }
+          }
+        }
+        if (resident) {
+          __syncthreads();
+#pragma unroll
+          for (int t = 0; t < kResRows; ++t) {
+            const int rr = tid + t * kThreads;
+            xr[t] = rr < crows_all ? xtmp[rr] : 0.0;
+            if (rr < crows_all) sl = fma(zr[t], xr[t], sl);
+          }
+        }
+      } else if (resident) {
 #pragma unroll
         for (int h = 0; h < kResRows / 4; ++h) {
           double xv[4];
@@ -649,7 +736,25 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     if (V == kNaive) {
       // p_i = A q_i with q_i = z_i / r_ii formed on the fly (Algorithm 4's second MV).
       const double* zsrc = (i > 0) ? zi : Z;
-      if (resident) {
+      if (a.mv_warp) {
+        const int lane = tid & 31, warp = tid >> 5;
+        double* ptmp = s_piv + (2 * cur + 1) * chunk;
+        for (int64_t k = k0 + warp; k < k1; k += kWarps) {
+          const double pk = csr_row_warp(rowptr, colidx, val, zsrc, inv, true, k);
+          if (lane == 0) {
+            if (resident) ptmp[k - k0] = pk;
+            else X[k + ldx] = pk;
+          }
+        }
+        if (resident) {
+          __syncthreads();
+#pragma unroll
+          for (int t = 0; t < kResRows; ++t) {
+            const int rr = tid + t * kThreads;
+            xr[t] = rr < crows_all ? ptmp[rr] : 0.0;
+          }
+        }
+      } else if (resident) {
 #pragma unroll
         for (int h = 0; h < kResRows / 4; ++h) {
           double pv[4];
@@ -824,6 +929,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_batch_kernel(const BatchArgs 
       a.ctl = nullptr;
       a.rpc = (m + 31) / 32 * 32;
       a.chunk = (int)(a.rpc < kMaxChunk ? a.rpc : kMaxChunk);
+      a.mv_warp = (int64_t)__ldg(J.rowptr + m) >= (int64_t)kWarpRowNnz * m;
       result = sweep_body<V, true>(a, 1, 0, smem, s_wfirst, s_wlast, s_flags);
     }
     if (threadIdx.x == 0) {

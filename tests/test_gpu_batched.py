@@ -46,6 +46,8 @@ def mixed_instances(count, seed=11, m_hi=6000, n_hi=64):
     out.append(W.banded(40, 40, seed=3))  # m = n
     out.append(W.banded(4096, 17, seed=4))  # largest resident slab
     out.append(W.banded(8200, 9, seed=5))   # two chunks
+    out.append(W.denseband(1500, 20, hb=60))  # long rows: warp-per-row MVs
+    out.append(W.denseband(6000, 12, hb=40))  # long rows, two chunks
     return out
 
 

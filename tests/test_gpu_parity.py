@@ -76,6 +76,9 @@ SMALL_CASES = {
     "banded_3000x64": lambda: W.banded(3000, 64, seed=4),
     "banded_20011x40": lambda: W.banded(20011, 40, seed=5),
     "varcoef3d_12": lambda: W.varcoef3d(side=12, n=24),
+    # long rows (warp-per-row MVs): 201 and 389 nonzeros per row
+    "denseband_2000x24": lambda: W.denseband(2000, 24, hb=100),
+    "denseband_9180x50": lambda: W.denseband(),
 }
 
 
@@ -213,3 +216,18 @@ def test_host_entry_point_matches_device(handle, variant):
                                  mgsa.VARIANTS[variant], Qh, 2500, Rh, 13)
     assert (st, info) == (mgsa.MGSA_OK, 0)
     assert np.array_equal(Qh, Qd) and np.array_equal(Rh, Rd)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_long_rows_multi_chunk(handle, variant):
+    """Warp-per-row MVs outside resident mode (two CTAs, several chunks each)."""
+    A, Z = W.denseband(9180, 20)
+    handle.set_param(mgsa.MGSA_PARAM_MAX_CTAS, 2)
+    handle.set_param(mgsa.MGSA_PARAM_CHUNK_ROWS, 1024)
+    try:
+        Q, R, st, info = gpu_qr(handle, A, Z, variant)
+    finally:
+        handle.set_param(mgsa.MGSA_PARAM_MAX_CTAS, 0)
+        handle.set_param(mgsa.MGSA_PARAM_CHUNK_ROWS, 0)
+    assert (st, info) == (mgsa.MGSA_OK, 0)
+    check_parity(A, Z, variant, Q, R)

@@ -24,7 +24,10 @@ families stand in for them):
                      U(-1, 1) mirrored, diagonal 1 + row |off-diagonal| sum;
 * ``batch``          4096 banded instances with m ~ logU[256, 8192],
                      n ~ U{4..64};
-* ``exp2``           Section 4.2's A = V D V^T, Z = U E W^T test family.
+* ``exp2``           Section 4.2's A = V D V^T, Z = U E W^T test family;
+* ``denseband``      banded SPD with half-bandwidth 194 and m = 9180: about
+                     389 nonzeros per row and 3.5e6 in all, the size and
+                     density of the sparse matrix of Section 4.1, Z = N(0,1).
 """
 from __future__ import annotations
 
@@ -186,6 +189,12 @@ def varcoef3d(side: int = 128, n: int = 128, seed: int = SEED, shift: float = 1e
 def banded(m: int, n: int, seed: int = SEED, hb: int = 8, index: int = 0):
     A = banded_spd_csr(m, hb, rng(seed, TAG_BAND, index))
     return A, gaussian_Z(m, n, seed, TAG_Z, index)
+
+
+def denseband(m: int = 9180, n: int = 50, hb: int = 194, seed: int = SEED):
+    """Dense-band SPD matrix (long CSR rows) and Gaussian Z."""
+    A = banded_spd_csr(m, hb, rng(seed, TAG_BAND, 194))
+    return A, gaussian_Z(m, n, seed, TAG_Z, 194)
 
 
 def batch_sizes(count: int = 4096, seed: int = SEED, m_lo: int = 256, m_hi: int = 8192, n_lo: int = 4, n_hi: int = 64):

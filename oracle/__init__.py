@@ -47,6 +47,9 @@ def _bind(lib):
     lib.oracle_mgs.restype = ctypes.c_int
     lib.oracle_mgs.argtypes = [i32, i32, i64, i32, ip, ip, dp, dp, i64, dp, i64, dp, i32,
                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_mgs_append.restype = ctypes.c_int
+    lib.oracle_mgs_append.argtypes = [i32, i64, i32, i32, ip, ip, dp, dp, i64, dp, i64, dp, i64, dp, i64, dp, i64, dp,
+                                      i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
     lib.oracle_csr_mv.restype = None
     lib.oracle_csr_mv.argtypes = [i64, ip, ip, dp, dp, dp]
     lib.oracle_repr_error.restype = None
@@ -96,6 +99,33 @@ def mgs(A, Z: np.ndarray, variant: str = "naive", form: str = "col", lib=None):
     if info < 0:
         raise ValueError("oracle_mgs: invalid arguments")
     return Q, R, int(info), int(kind.value), int(mv.value)
+
+
+def mgs_append(A, Qo, Po, Z: np.ndarray, variant: str = "naive", lib=None):
+    """Successive orthogonalisation: continue Algorithm 3/5/6 (column form)
+    with k given columns ``Qo`` (A-orthonormal) and ``Po`` (their p_i), then
+    the n columns of ``Z``.  Returns ``(Q, P, R, info, kind, mv_count)`` with
+    R of shape (k+n, n).  ``Qo = Po = None`` (k = 0) is Algorithm 3/5/6."""
+    lib = lib or load()
+    rowptr, col, val = _csr_arrays(A)
+    Zf = _fortran(Z)
+    m, n = Zf.shape
+    if Qo is None:
+        k, Qof, Pof = 0, np.zeros((m, 1), order="F"), np.zeros((m, 1), order="F")
+    else:
+        Qof, Pof = _fortran(Qo), _fortran(Po)
+        k = Qof.shape[1]
+    Q = np.zeros((m, n), dtype=np.float64, order="F")
+    P = np.zeros((m, n), dtype=np.float64, order="F")
+    R = np.zeros((k + n, n), dtype=np.float64, order="F")
+    mv = ctypes.c_int64(0)
+    kind = ctypes.c_int(0)
+    info = lib.oracle_mgs_append(VARIANTS[variant], m, k, n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(Qof), m,
+                                 _ptr(Pof), m, _ptr(Zf), m, _ptr(Q), m, _ptr(P), m, _ptr(R), k + n,
+                                 ctypes.byref(mv), ctypes.byref(kind))
+    if info < 0:
+        raise ValueError("oracle_mgs_append: invalid arguments")
+    return Q, P, R, int(info), int(kind.value), int(mv.value)
 
 
 def csr_mv(A, x: np.ndarray, lib=None) -> np.ndarray:

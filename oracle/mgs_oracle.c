@@ -332,6 +332,75 @@ int oracle_mgs_hp_row(int64_t m, int n, const int32_t* rowptr, const int32_t* co
   return info;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Successive orthogonalisation (Section 2.1: the column-oriented MGS is   */
+/* the one suited to it).  Given k columns Qo (m x k) that are already     */
+/* A-orthonormal and Po (= A Qo as the algorithm produced it), the n new    */
+/* columns Z are A-orthonormalised against them and among themselves by     */
+/* continuing Algorithm 3 (naive), 5 (HA) or 6 (HP) at column k+1.         */
+/* Outputs: Q (m x n), P (m x n, the p_j of the new columns), R ((k+n) x n, */
+/* column-major, ldr >= k+n: rows 0..k-1 hold r_ij against the old columns, */
+/* rows k..k+n-1 the new upper triangle).  With k = 0 this is Algorithm     */
+/* 3 / 5 / 6 itself, and appending to the result of the first k columns     */
+/* performs exactly the operations of one run over all k + n columns.      */
+/* ---------------------------------------------------------------------- */
+int oracle_mgs_append(int variant, int64_t m, int k, int n, const int32_t* rowptr, const int32_t* col,
+                      const double* val, const double* Qo, int64_t ldqo, const double* Po, int64_t ldpo,
+                      const double* Z, int64_t ldz, double* Q, int64_t ldq, double* P, int64_t ldp, double* R,
+                      int ldr, int64_t* mv_count, int* kind) {
+  if (m < 1 || n < 1 || k < 0 || m < k + n || ldz < m || ldq < m || ldp < m || ldr < k + n) return -1;
+  if (k > 0 && (!Qo || !Po || ldqo < m || ldpo < m)) return -1;
+  double* X = (variant == 2) ? (double*)malloc(sizeof(double) * (size_t)m * (size_t)n) : NULL;
+  double* x = (double*)malloc(sizeof(double) * (size_t)m);
+  int info = 0;
+  *kind = 0;
+  *mv_count = 0;
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < k + n; ++i) R[i + (int64_t)j * ldr] = 0.0;
+  copy_cols(m, n, Z, ldz, Q, ldq);
+  if (variant == 2) {
+    for (int j = 0; j < n; ++j) csr_mv(m, rowptr, col, val, QC(j), X + (int64_t)j * m); /* X = A Z */
+    *mv_count = 1;
+  }
+  for (int j = 0; j < n && !info; ++j) {
+    double* zj = QC(j);
+    /* r_ij and z_j^{(i)} against the old columns, then the new ones (ascending i) */
+    for (int i = 0; i < k; ++i) {
+      R[i + (int64_t)j * ldr] = dot(m, Po + (int64_t)i * ldpo, zj);
+      axpy_sub(m, R[i + (int64_t)j * ldr], Qo + (int64_t)i * ldqo, zj);
+    }
+    for (int i = 0; i < j; ++i) {
+      R[k + i + (int64_t)j * ldr] = dot(m, P + (int64_t)i * ldp, zj);
+      axpy_sub(m, R[k + i + (int64_t)j * ldr], QC(i), zj);
+    }
+    const double* xj;
+    if (variant == 2) {
+      double* xw = X + (int64_t)j * m; /* x_j^{(j-1)} = x_j^{(0)} - sum_i r_ij p_i (eq. (tec2)) */
+      for (int i = 0; i < k; ++i) axpy_sub(m, R[i + (int64_t)j * ldr], Po + (int64_t)i * ldpo, xw);
+      for (int i = 0; i < j; ++i) axpy_sub(m, R[k + i + (int64_t)j * ldr], P + (int64_t)i * ldp, xw);
+      xj = xw;
+    } else {
+      csr_mv(m, rowptr, col, val, zj, x); /* x_j^{(j-1)} = A z_j^{(j-1)} */
+      ++*mv_count;
+      xj = x;
+    }
+    double s = dot(m, zj, xj);
+    if (!diag_ok(s, kind)) { info = j + 1; break; }
+    const double r = sqrt(s);
+    R[k + j + (int64_t)j * ldr] = r;
+    scale_div(m, zj, r, zj); /* q_j */
+    if (variant == 0) {
+      csr_mv(m, rowptr, col, val, zj, P + (int64_t)j * ldp); /* p_j = A q_j */
+      ++*mv_count;
+    } else {
+      scale_div(m, xj, r, P + (int64_t)j * ldp); /* p_j = x_j / r_jj (eq. (tec1)) */
+    }
+  }
+  free(X);
+  free(x);
+  return info;
+}
+
 /* Dispatcher: variant 0 = naive, 1 = HA, 2 = HP; form 0 = col, 1 = row. */
 int oracle_mgs(int variant, int form, int64_t m, int n, const int32_t* rowptr, const int32_t* col,
                const double* val, const double* Z, int64_t ldz, double* Q, int64_t ldq, double* R, int ldr,

@@ -146,6 +146,37 @@ mgsa_status mgsa_qr_host(mgsa_handle h, const int32_t* rowptr, const int32_t* co
                          int64_t nnz, const double* Z, int64_t m, int n, int64_t ldz, mgsa_variant v,
                          double* Q, int64_t ldq, double* R, int ldr, mgsa_stream_t s, int* info);
 
+/* Successive orthogonalisation (Section 2: the column-oriented, left-looking
+ * MGS suits orthogonalising new columns against ones already orthonormalised).
+ * Given k columns Qold (A-orthonormal) and Pold = A Qold (the p_i of the run
+ * that produced them), orthonormalise the n columns of Z against them and
+ * among themselves in the form `v`:
+ *
+ *   [Qold Z] = [Qold Q] [ I  R_top ]     R = [ R_top ]   (k + n) x n
+ *                       [ 0  R_bot ]         [ R_bot ]
+ *
+ * with Q^T A Q = I, Qold^T A Q = 0 (in exact arithmetic); R_bot is upper
+ * triangular.  The result equals mgsa_qr on [Qold Z] with the first k pivots
+ * taken as given (one device-wide step per given column, no MV for it).
+ *
+ *   Qold, Pold  m x k device arrays, leading dimensions ldqo, ldpo >= m
+ *               (read only; may be NULL when k == 0).  The p_i the form uses
+ *               are Pold's columns as given (HA / naive / HP alike).
+ *   Z, Q, A, s  as for mgsa_qr.
+ *   P           m x n output p_j = A q_j of the new columns as the form forms
+ *               them (naive: A q_j; HA / HP: the recurrence of eq. (tec1)),
+ *               leading dimension ldp >= m; NULL = not returned.  Passing the
+ *               (Q, P) of one call as (Qold, Pold) of the next grows a basis.
+ *   R           (k + n) x n output, leading dimension ldr >= k + n.
+ *
+ * Requirements: 0 <= k, 1 <= n, k + n <= MGSA_MAX_N, k + n <= m < 2^31; no
+ * output overlaps an input or another output.  Status and info as for
+ * mgsa_qr (info counts the columns of Z, 1-based).  mgsa_reserve(h, m, k + n,
+ * v) makes the call allocation-free. */
+mgsa_status mgsa_qr_append(mgsa_handle h, const mgsa_csr* A, const double* Qold, int64_t ldqo, const double* Pold,
+                           int64_t ldpo, int k, const double* Z, int64_t m, int n, int64_t ldz, mgsa_variant v,
+                           double* Q, int64_t ldq, double* P, int64_t ldp, double* R, int ldr, mgsa_stream_t s);
+
 /* ---------------------------------------------------------------------- */
 /* Batched QR: many independent instances in one call.                      */
 /* ---------------------------------------------------------------------- */

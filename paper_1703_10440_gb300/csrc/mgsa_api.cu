@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstddef>
 #include <cstring>
+#include <utility>
 
 #include "mgsa.h"
 #include "mgsa_internal.cuh"
@@ -73,13 +74,17 @@ struct Plan {
 };
 
 // nnz < 0: unknown (workspace sizing); long rows (warp-per-row MVs) carry
-// more work per row, so they get smaller slabs and thus more CTAs.
-mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, Plan* p, int64_t nnz = -1) {
+// more work per row, so they get smaller slabs and thus more CTAs.  kg given
+// columns in front (successive orthogonalisation) widen the shared rows and
+// partial sums to kg + n columns; the X columns stay those of the n new ones.
+mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, Plan* p, int64_t nnz = -1,
+                      int kg = 0) {
+  const int nt = kg + n;
   const int chunk_cap = h->chunk_rows > 0 ? h->chunk_rows : mgsa::kMaxChunk;
   const bool long_rows = nnz >= (int64_t)mgsa::kWarpRowNnz * m;
   const int64_t min_rows = h->min_rows > 0 ? h->min_rows : (long_rows ? mgsa::kMinRowsLongRows : mgsa::kMinRowsPerCta);
   int max_ctas = 0;
-  cudaError_t e = mgsa::sweep_max_ctas((int)v, mgsa::sweep_smem_bytes(n, chunk_cap), &max_ctas);
+  cudaError_t e = mgsa::sweep_max_ctas((int)v, mgsa::sweep_smem_bytes(nt, chunk_cap), &max_ctas);
   if (e != cudaSuccess) return cuda_fail(e);
   if (max_ctas < 1) return fail(MGSA_ERR_CUDA, "sweep kernel does not fit on this device");
   int64_t g = std::min<int64_t>(max_ctas, (m + min_rows - 1) / min_rows);
@@ -88,12 +93,12 @@ mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, P
   p->rpc = round_up((m + g - 1) / g, 32);
   p->grid = (int)((m + p->rpc - 1) / p->rpc);
   p->chunk = (int)std::min<int64_t>(chunk_cap, p->rpc);
-  p->smem = mgsa::sweep_smem_bytes(n, p->chunk);
+  p->smem = mgsa::sweep_smem_bytes(nt, p->chunk);
   p->ldx = round_up(m, 32);
   p->xcols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
   p->x_bytes = (size_t)round_up((int64_t)sizeof(double) * p->ldx * p->xcols, 256);
   // Partials for the largest grid any plan can use, so a reservation fits every nnz.
-  p->part_bytes = sizeof(double) * (size_t)(2 * n + 1) * (size_t)std::max<int64_t>(max_ctas, p->grid);
+  p->part_bytes = sizeof(double) * (size_t)(2 * nt + 1) * (size_t)std::max<int64_t>(max_ctas, p->grid);
   return MGSA_OK;
 }
 
@@ -214,26 +219,52 @@ mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value) {
   }
 }
 
-mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
-                    mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, mgsa_stream_t s) {
+// Checks shared by mgsa_qr and mgsa_qr_append, then one cooperative launch.
+// kg given columns Qg (with their p_i in Pg) precede the n columns of Z; P
+// (nullable) receives the p_j of the new columns.
+static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
+                             mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, int kg, const double* Qg,
+                             int64_t ldqg, const double* Pg, int64_t ldpg, double* P, int64_t ldp, mgsa_stream_t s) {
   if (!h) return fail(MGSA_ERR_INVALID, "NULL handle");
   if (!A || !Z || !Q || !R) return fail(MGSA_ERR_INVALID, "NULL matrix pointer");
-  mgsa_status st = check_sizes(m, n, ldz, v, ldq, ldr);
+  if (kg < 0 || kg > MGSA_MAX_N - 1) return fail(MGSA_ERR_INVALID, "k must be in [0, MGSA_MAX_N)");
+  mgsa_status st = check_sizes(m, n, ldz, v, ldq, n);  // ldr is checked against k + n below
   if (st != MGSA_OK) return st;
+  const int nt = kg + n;
+  if (nt > MGSA_MAX_N) return fail(MGSA_ERR_INVALID, "k + n must be <= MGSA_MAX_N");
+  if (m < nt) return fail(MGSA_ERR_INVALID, "m must be >= k + n");
+  if (ldr < nt) return fail(MGSA_ERR_INVALID, "leading dimension of R below k + n");
+  if (kg > 0) {
+    if (!Qg || !Pg) return fail(MGSA_ERR_INVALID, "NULL given Q or P");
+    if (ldqg < m || ldpg < m) return fail(MGSA_ERR_INVALID, "leading dimension of the given Q or P below m");
+  }
+  if (P && ldp < m) return fail(MGSA_ERR_INVALID, "leading dimension of P below m");
   if (A->m != m) return fail(MGSA_ERR_INVALID, "A->m differs from m");
   if (A->nnz < 0 || A->nnz >= ((int64_t)1 << 31)) return fail(MGSA_ERR_INVALID, "nnz must be in [0, 2^31)");
   if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return fail(MGSA_ERR_INVALID, "NULL CSR array");
   const size_t zspan = sizeof(double) * (size_t)((n - 1) * ldz + m);
   const size_t qspan = sizeof(double) * (size_t)((n - 1) * ldq + m);
   if (ranges_overlap(Z, zspan, Q, qspan)) return fail(MGSA_ERR_INVALID, "Q overlaps Z");
-  const size_t rspan = sizeof(double) * (size_t)((int64_t)(n - 1) * ldr + n);
+  const size_t rspan = sizeof(double) * (size_t)((int64_t)(n - 1) * ldr + nt);
   if (ranges_overlap(R, rspan, Q, qspan) || ranges_overlap(R, rspan, Z, zspan))
     return fail(MGSA_ERR_INVALID, "R overlaps Q or Z");
+  const size_t pspan = P ? sizeof(double) * (size_t)((n - 1) * ldp + m) : 0;
+  if (P && (ranges_overlap(P, pspan, Q, qspan) || ranges_overlap(P, pspan, Z, zspan) ||
+            ranges_overlap(P, pspan, R, rspan)))
+    return fail(MGSA_ERR_INVALID, "P overlaps Q, Z or R");
+  if (kg > 0) {
+    const size_t gq = sizeof(double) * (size_t)((kg - 1) * ldqg + m);
+    const size_t gp = sizeof(double) * (size_t)((kg - 1) * ldpg + m);
+    for (const auto& o : {std::make_pair((const void*)Q, qspan), std::make_pair((const void*)R, rspan),
+                          std::make_pair((const void*)P, pspan)})
+      if (o.second && (ranges_overlap(Qg, gq, o.first, o.second) || ranges_overlap(Pg, gp, o.first, o.second)))
+        return fail(MGSA_ERR_INVALID, "an output overlaps the given Q or P");
+  }
 
   DeviceGuard g(h->device);
   if (!g.ok) return fail(MGSA_ERR_CUDA, "cannot select the device");
   Plan p;
-  if ((st = make_plan(h, m, n, v, &p, A->nnz)) != MGSA_OK) return st;
+  if ((st = make_plan(h, m, n, v, &p, A->nnz, kg)) != MGSA_OK) return st;
   if ((st = ensure_ws(h, p.x_bytes + p.part_bytes)) != MGSA_OK) return st;
 
   mgsa::SweepArgs a;
@@ -255,6 +286,18 @@ mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m
   a.rpc = p.rpc;
   a.chunk = p.chunk;
   a.mv_warp = A->nnz >= (int64_t)mgsa::kWarpRowNnz * m;
+  a.kg = kg;
+  a.Qg = Qg;
+  a.ldqg = ldqg;
+  a.Pg = Pg;
+  a.ldpg = ldpg;
+  if (P && v == MGSA_HP) {
+    a.X = P;  // HP keeps x_j, then p_j, in X: let them land in P directly
+    a.ldx = ldp;
+  } else {
+    a.Pout = P;
+    a.ldpo = ldp;
+  }
 
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
   cudaError_t e = cudaMemsetAsync(h->ctl, 0, sizeof(int) * mgsa::kCtlWords, cs);
@@ -262,6 +305,17 @@ mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m
   e = mgsa::sweep_launch((int)v, a, p.grid, p.smem, cs);
   if (e != cudaSuccess) return cuda_fail(e);
   return MGSA_OK;
+}
+
+mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
+                    mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, mgsa_stream_t s) {
+  return qr_launch(h, A, Z, m, n, ldz, v, Q, ldq, R, ldr, 0, nullptr, 0, nullptr, 0, nullptr, 0, s);
+}
+
+mgsa_status mgsa_qr_append(mgsa_handle h, const mgsa_csr* A, const double* Qold, int64_t ldqo, const double* Pold,
+                           int64_t ldpo, int k, const double* Z, int64_t m, int n, int64_t ldz, mgsa_variant v,
+                           double* Q, int64_t ldq, double* P, int64_t ldp, double* R, int ldr, mgsa_stream_t s) {
+  return qr_launch(h, A, Z, m, n, ldz, v, Q, ldq, R, ldr, k, Qold, ldqo, Pold, ldpo, P, ldp, s);
 }
 
 size_t mgsa_job_workspace_bytes(int64_t m, int n, mgsa_variant v) {

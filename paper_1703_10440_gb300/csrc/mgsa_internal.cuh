@@ -36,11 +36,21 @@ struct SweepArgs {
   int ldr;
   double* X;       // HP: m x n (x_j, then p_j); HA: x_i in column 0; naive: x_i, p_i in columns 0, 1
   int64_t ldx;
-  double* part;    // (2n + 1) * G partial sums: dots [parity][b][j] (two step-parity buffers), then norm [b]
+  double* part;    // (2(kg+n) + 1) * G partial sums: dots [parity][b][j] (two step-parity buffers), then norm [b]
   int* ctl;        // control block (CtlWord)
   int64_t rpc;     // rows per CTA, multiple of 32
   int chunk;       // rows per staged chunk, multiple of 32
   int mv_warp;     // 1: one warp per CSR row in the MVs / block product (long rows)
+  // Successive orthogonalisation: kg given A-orthonormal columns Qg (with Pg =
+  // their p_i) come first; the n columns of Z are columns kg .. kg+n-1 of the
+  // virtual matrix and R is (kg+n) x n.  kg = 0 for a plain QR.
+  int kg = 0;
+  const double* Qg = nullptr;
+  int64_t ldqg = 0;
+  const double* Pg = nullptr;
+  int64_t ldpg = 0;
+  double* Pout = nullptr;  // optional p_j of the new columns (HA / naive; HP keeps them in X)
+  int64_t ldpo = 0;
 };
 
 // Average row length from which a warp, not a thread, takes one CSR row.

@@ -225,45 +225,46 @@ __device__ void diagonal(const double* part_norm, int G, double* s_scal) {
   __syncthreads();
 }
 
-// r_{i,i+1}: the first entry of row i right of the diagonal (warp 0).
-__device__ void reduce_first(const double* part, int G, int n, int i, double* s_rrow, double* R, int ldr,
+// r_{i,i+1}: the first entry of row i right of the diagonal (warp 0).  Column
+// j of the virtual matrix is column j - kg of R.
+__device__ void reduce_first(const double* part, int G, int nt, int i, double* s_rrow, double* R, int ldr, int kg,
                              bool write_r) {
   if (threadIdx.x < 32) {
-    const double r = warp0_sum_ctas(part + (i + 1), n, G);
+    const double r = warp0_sum_ctas(part + (i + 1), nt, G);
     if (threadIdx.x == 0) {
       s_rrow[i + 1] = r;
-      if (write_r) R[i + (int64_t)(i + 1) * ldr] = r;
+      if (write_r) R[i + (int64_t)(i + 1 - kg) * ldr] = r;
     }
   }
   __syncthreads();
 }
 
-// r_ij for j = i+2 .. n-1, lane per column: warp w adds the partials of the
-// CTAs in [w*G/16, (w+1)*G/16) in order, then warp 0 adds the 16 warp sums in
-// order.  Loads are coalesced because part is laid out [CTA][column].
-__device__ void reduce_rest(const double* part, int G, int n, int i, double* s_rrow, double* s_buf, double* R,
-                            int ldr, bool write_r) {
+// r_ij for j = jstart .. nt-1, lane per column: warp w adds the partials of
+// the CTAs in [w*G/16, (w+1)*G/16) in order, then warp 0 adds the 16 warp sums
+// in order.  Loads are coalesced because part is laid out [CTA][column].
+__device__ void reduce_rest(const double* part, int G, int nt, int i, int jstart, double* s_rrow, double* s_buf,
+                            double* R, int ldr, int kg, bool write_r) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int bb0 = (int)((int64_t)G * warp / kWarps), bb1 = (int)((int64_t)G * (warp + 1) / kWarps);
-  for (int j0 = i + 2; j0 < n; j0 += 32) {
+  for (int j0 = jstart; j0 < nt; j0 += 32) {
     const int j = j0 + lane;
     double t0 = 0.0, t1 = 0.0;
     int bb = bb0;
     for (; bb + 1 < bb1; bb += 2) {
-      const double v0 = j < n ? ld_cg(part + (int64_t)bb * n + j) : 0.0;
-      const double v1 = j < n ? ld_cg(part + (int64_t)(bb + 1) * n + j) : 0.0;
+      const double v0 = j < nt ? ld_cg(part + (int64_t)bb * nt + j) : 0.0;
+      const double v1 = j < nt ? ld_cg(part + (int64_t)(bb + 1) * nt + j) : 0.0;
       t0 += v0;
       t1 += v1;
     }
-    if (bb < bb1) t0 += j < n ? ld_cg(part + (int64_t)bb * n + j) : 0.0;
+    if (bb < bb1) t0 += j < nt ? ld_cg(part + (int64_t)bb * nt + j) : 0.0;
     s_buf[threadIdx.x] = t0 + t1;
     __syncthreads();
-    if (warp == 0 && j < n) {
+    if (warp == 0 && j < nt) {
       double t = s_buf[lane];
 #pragma unroll
       for (int w = 1; w < kWarps; ++w) t += s_buf[lane + 32 * w];
       s_rrow[j] = t;
-      if (write_r) R[i + (int64_t)j * ldr] = t;
+      if (write_r) R[i + (int64_t)(j - kg) * ldr] = t;
     }
     __syncthreads();
   }
@@ -322,19 +323,19 @@ __device__ __forceinline__ double csr_row_warp(const int32_t* __restrict__ rowpt
 }
 
 // The fused pass over one chunk of rows [c0, c0 + crows) and the columns
-// j = i+1 .. n-1: apply step i-1's updates z_j -= r_{i-1,j} q_{i-1} (HP:
+// j = jbeg .. jbeg+ncols-1: apply step i-1's updates z_j -= r_{i-1,j} q_{i-1} (HP:
 // x_j -= r_{i-1,j} p_{i-1}) and accumulate p_i^T z_j.  Work units are
 // (column, 32-row block) pairs split into equal contiguous ranges, one per
 // warp; each warp reduces each of its column pieces with a butterfly and the
 // pieces are added in warp order into s_racc.  Pivots come from shared
 // memory: s_qprev = q_{i-1}, s_pprev = p_{i-1}, s_pcur = p_i.
 template <int V>
-__device__ __forceinline__ void fused_pass(int i, int n, int64_t c0, int crows, const double* s_qprev,
-                                           const double* s_pprev, const double* s_pcur, const double* s_rrow,
-                                           double* __restrict__ Q, int64_t ldq, double* __restrict__ X, int64_t ldx,
-                                           double* s_piece, int kmax, int* s_wfirst, int* s_wlast, double* s_racc) {
+__device__ __forceinline__ void fused_pass(int i, int jbeg, int ncols, int kg, int64_t c0, int crows,
+                                           const double* s_qprev, const double* s_pprev, const double* s_pcur,
+                                           const double* s_rrow, double* __restrict__ Q, int64_t ldq,
+                                           double* __restrict__ X, int64_t ldx, double* s_piece, int kmax,
+                                           int* s_wfirst, int* s_wlast, double* s_racc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ncols = n - 1 - i;
   const int nb = (crows + 31) >> 5;
   const int U = ncols * nb;  // <= 2047 * 128
   int u = (int)((int64_t)U * warp / kWarps);
@@ -346,11 +347,11 @@ __device__ __forceinline__ void fused_pass(int i, int n, int64_t c0, int crows, 
   }
   while (u < u1) {
     const int jr = u / nb;
-    const int j = i + 1 + jr;
+    const int j = jbeg + jr;  // column of the virtual matrix; column j - kg of Q / X
     const int uend = (jr + 1) * nb < u1 ? (jr + 1) * nb : u1;
     const double rp = (i > 0) ? s_rrow[j] : 0.0;
-    double* zc = Q + (int64_t)j * ldq + c0;
-    double* xc = (V == kHP) ? X + (int64_t)j * ldx + c0 : X;
+    double* zc = Q + (int64_t)(j - kg) * ldq + c0;
+    double* xc = (V == kHP) ? X + (int64_t)(j - kg) * ldx + c0 : X;
     double acc0 = 0.0, acc1 = 0.0;
     const int rbeg = (u - jr * nb) * 32 + lane;
     int rend = (uend - jr * nb) * 32;
@@ -401,14 +402,16 @@ __device__ __forceinline__ void fused_pass(int i, int n, int64_t c0, int crows, 
 template <int V, bool kBatch>
 __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* smem, int* s_wfirst, int* s_wlast,
                           int* s_flags) {
-  const int n = a.n;
+  const int n = a.n;    // columns of Z
+  const int kg = a.kg;  // given columns before them (successive orthogonalisation)
+  const int nt = kg + n;
   const int chunk = a.chunk;
-  const int kmax = (n + kWarps - 1) / kWarps + 2;
+  const int kmax = (nt + kWarps - 1) / kWarps + 2;
   double* s_piv = smem;                      // 4 x chunk pivot rows
   double* s_piece = s_piv + 4 * chunk;       // kWarps x kmax warp pieces
   double* s_racc = s_piece + kWarps * kmax;  // CTA partials of the current row (relative column)
-  double* s_rrow = s_racc + n;               // r_{i-1, j} during step i, then r_{i, j}
-  double* s_buf = s_rrow + n;                // kThreads + 1 reduction scratch
+  double* s_rrow = s_racc + nt;              // r_{i-1, j} during step i, then r_{i, j}
+  double* s_buf = s_rrow + nt;               // kThreads + 1 reduction scratch
   double* s_scal = s_buf + kThreads + 1;     // r_ii, 1/r_ii, status
 
   const int tid = threadIdx.x;
@@ -429,15 +432,21 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
   double* __restrict__ R = a.R;
   const int64_t ldz = a.ldz, ldq = a.ldq, ldx = a.ldx;
   const int ldr = a.ldr;
-  // part: two buffers (step parity) of G x n dot partials, then G norm partials.
-  double* part_norm = a.part + 2 * (int64_t)n * G;
+  // part: two buffers (step parity) of G x nt dot partials, then G norm partials.
+  double* part_norm = a.part + 2 * (int64_t)nt * G;
+  // Column j >= kg of the virtual matrix lives in column j - kg of Q and X, and
+  // of R; the pivots of the given steps i < kg come from Qg and Pg.
+  auto zcol = [&](int j) { return Q + (int64_t)(j - kg) * ldq; };
+  auto xcol = [&](int j) { return X + (int64_t)(j - kg) * ldx; };
+  auto qsrc = [&](int i) -> const double* { return i < kg ? a.Qg + (int64_t)i * a.ldqg : zcol(i); };
+  auto psrc = [&](int i) -> const double* { return i < kg ? a.Pg + (int64_t)i * a.ldpg : xcol(i); };
   unsigned int gen = 0;
 
   MGSA_TRACE(4100, 0);
   // ---- Phase 0: R = 0; Q = Z on own rows; HP: X = A Z (one block product,
   // Algorithm 8 first line) and, outside resident mode, the partial z_1^T x_1. ----
   if (b == 0) {
-    for (int64_t t = tid; t < (int64_t)n * n; t += kThreads) R[(t % n) + (t / n) * ldr] = 0.0;
+    for (int64_t t = tid; t < (int64_t)nt * n; t += kThreads) R[(t % nt) + (t / nt) * ldr] = 0.0;
   }
   if (V == kHP && a.mv_warp) {
     // X = A Z with one warp per (long) row, kPanel columns at a time: lanes
@@ -541,19 +550,25 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
   __syncthreads();
   MGSA_TRACE(4100, 1);
 
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < nt; ++i) {
     MGSA_TRACE(i, 0);
     const int cur = i & 1, prev = cur ^ 1;
-    double* zi = Q + (int64_t)i * ldq;
-    const double* part_prev = a.part + (int64_t)prev * n * G;  // partials of row i-1
-    double* part_cur = a.part + (int64_t)cur * n * G;          // partials of row i
+    const bool given = i < kg;  // pivot q_i, p_i given (successive orthogonalisation)
+    double* zi = given ? nullptr : zcol(i);
+    const double* part_prev = a.part + (int64_t)prev * nt * G;  // partials of row i-1
+    double* part_cur = a.part + (int64_t)cur * nt * G;          // partials of row i
+    // The rest of row i-1 is summed during this step's first wait, unless row
+    // i-1 was a given step's (summed in full right away).
+    const bool rest_prev = i > kg;
     // This thread's rows tid + t*kThreads of z_i and x_i (naive: p_i), resident mode only.
     double zr[kResRows], xr[kResRows];
     // ---------------- column i: r_ii = sqrt(z_i^T x_i) ----------------
+    double inv = 0.0;
+    if (!given) {
     if (V == kHP) {
       if (resident) {
         const double r = (i > 0) ? s_rrow[i] : 0.0;  // r_{i-1,i}
-        const double* xi = X + (int64_t)i * ldx;
+        const double* xi = xcol(i);
         const double* sq = s_piv + 2 * prev * chunk;
         const double* sp = sq + chunk;
 #pragma unroll
@@ -579,9 +594,9 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       } else if (i > 0) {
         const double r = s_rrow[i];  // r_{i-1,i}
         double sl = 0.0;
-        double* xi = X + (int64_t)i * ldx;
-        const double* qp = Q + (int64_t)(i - 1) * ldq;
-        const double* pp = X + (int64_t)(i - 1) * ldx;
+        double* xi = xcol(i);
+        const double* qp = qsrc(i - 1);
+        const double* pp = psrc(i - 1);
         // Four rows per thread per trip, loads first (rows stay in ascending order).
         for (int64_t k = k0 + tid; k < k1; k += 4 * kThreads) {
           double zz[4], xx[4], qq[4], pv[4];
@@ -611,13 +626,13 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       }
       MGSA_TRACE(i, 1);
       sync_arrive<kBatch>(a.ctl, gen, s_flags);
-      if (i > 0) reduce_rest(part_prev, G, n, i - 1, s_rrow, s_buf, R, ldr, b == 0);  // r_{i-1,j}, j > i
+      if (rest_prev) reduce_rest(part_prev, G, nt, i - 1, i + 1, s_rrow, s_buf, R, ldr, kg, b == 0);  // r_{i-1,j>i}
       if (!sync_wait<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     } else {
       const double* zsrc;  // column i of the working Z, complete on every row
       if (i > 0) {
         const double r = s_rrow[i];
-        const double* qp = Q + (int64_t)(i - 1) * ldq;
+        const double* qp = qsrc(i - 1);
         if (resident) {
           const double* sq = s_piv + 2 * prev * chunk;
 #pragma unroll
@@ -650,7 +665,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
           }
         }
         sync_arrive<kBatch>(a.ctl, gen, s_flags);
-        reduce_rest(part_prev, G, n, i - 1, s_rrow, s_buf, R, ldr, b == 0);  // r_{i-1,j}, j > i
+        if (rest_prev) reduce_rest(part_prev, G, nt, i - 1, i + 1, s_rrow, s_buf, R, ldr, kg, b == 0);
         if (!sync_wait<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
         zsrc = zi;
       } else {
@@ -729,9 +744,9 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     MGSA_TRACE(i, 2);
     diagonal(part_norm, G, s_scal);
     MGSA_TRACE(i, 3);
-    if (s_scal[2] != 0.0) return body_result((int)s_scal[2], i + 1);  // the same verdict in every CTA
-    const double inv = s_scal[1];
-    if (b == 0 && tid == 0) R[i + (int64_t)i * ldr] = s_scal[0];
+    if (s_scal[2] != 0.0) return body_result((int)s_scal[2], i + 1 - kg);  // the same verdict in every CTA
+    inv = s_scal[1];
+    if (b == 0 && tid == 0) R[i + (int64_t)(i - kg) * ldr] = s_scal[0];
 
     if (V == kNaive) {
       // p_i = A q_i with q_i = z_i / r_ii formed on the fly (Algorithm 4's second MV).
@@ -776,9 +791,11 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       // Other CTAs still gather z_i; q_i may overwrite it only after this wait.
       if (!sync_all<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     }
+    }  // !given
 
     // ---------------- fused pass ----------------
-    const int ncols = n - 1 - i;
+    const int jbeg = i + 1 > kg ? i + 1 : kg;  // first working column right of pivot i
+    const int ncols = nt - jbeg;
     for (int jr = tid; jr < ncols; jr += kThreads) s_racc[jr] = 0.0;
     if (resident) {
       // q_i = z_i / r_ii and p_i (eq. (tec1); naive: A q_i) from registers into
@@ -792,10 +809,16 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         if (rr < nb32) {
           double qv = 0.0, pv = 0.0;
           if (rr < crows_all) {
-            qv = zr[t] * inv;
-            zi[k0 + rr] = qv;
-            pv = (V == kNaive) ? xr[t] : xr[t] * inv;
-            if (V == kHP) X[k0 + rr + (int64_t)i * ldx] = pv;
+            if (given) {
+              qv = a.Qg[k0 + rr + (int64_t)i * a.ldqg];
+              pv = a.Pg[k0 + rr + (int64_t)i * a.ldpg];
+            } else {
+              qv = zr[t] * inv;
+              zi[k0 + rr] = qv;
+              pv = (V == kNaive) ? xr[t] : xr[t] * inv;
+              if (V == kHP) xcol(i)[k0 + rr] = pv;
+              else if (a.Pout) a.Pout[k0 + rr + (int64_t)(i - kg) * a.ldpo] = pv;
+            }
           }
           sqc[rr] = qv;
           spc[rr] = pv;
@@ -805,16 +828,17 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       MGSA_TRACE(i, 4);
       if (ncols > 0) {
         const double* sqp = s_piv + 2 * prev * chunk;
-        fused_pass<V>(i, n, k0, crows_all, sqp, sqp + chunk, spc, s_rrow, Q, ldq, X, ldx, s_piece, kmax, s_wfirst,
-                      s_wlast, s_racc);
+        fused_pass<V>(i, jbeg, ncols, kg, k0, crows_all, sqp, sqp + chunk, spc, s_rrow, Q, ldq, X, ldx, s_piece, kmax,
+                      s_wfirst, s_wlast, s_racc);
       }
     } else {
       double* s_qprev = s_piv;
       double* s_pprev = s_piv + chunk;
       double* s_pcur = s_piv + 2 * chunk;
-      const double* const qprev = Q + (int64_t)(i > 0 ? i - 1 : 0) * ldq;
-      const double* const pprev = (V == kHP) ? X + (int64_t)(i > 0 ? i - 1 : 0) * ldx : X;
-      const double* xsrc = (V == kHP) ? X + (int64_t)i * ldx : (V == kHA ? X : X + ldx);
+      const double* const qprev = i > 0 ? qsrc(i - 1) : Q;
+      const double* const pprev = (V == kHP && i > 0) ? psrc(i - 1) : X;
+      const double* const qgiv = given ? qsrc(i) : Q;
+      const double* xsrc = given ? psrc(i) : ((V == kHP) ? xcol(i) : (V == kHA ? X : X + ldx));
       for (int64_t c0 = k0; c0 < k1; c0 += chunk) {
         const int crows = (int)((k1 - c0) < chunk ? (k1 - c0) : chunk);
         const int nb = (crows + 31) >> 5;
@@ -827,7 +851,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
             const int r = r0 + q * kThreads;
             const bool ok = r < crows;
             const int64_t k = c0 + r;
-            zv[q] = ok ? zi[k] : 0.0;
+            zv[q] = ok ? (given ? qgiv[k] : zi[k]) : 0.0;
             xv[q] = ok ? xsrc[k] : 0.0;
             qv[q] = (ok && i > 0) ? qprev[k] : 0.0;
             pv[q] = (ok && i > 0 && V == kHP) ? pprev[k] : 0.0;
@@ -837,15 +861,18 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
             const int r = r0 + q * kThreads;
             if (r < nb * 32) {
               double pc = 0.0;
-              if (r < crows) {
+              if (r < crows && given) {
+                pc = xv[q];  // given p_i
+              } else if (r < crows) {
                 const int64_t k = c0 + r;
                 zi[k] = zv[q] * inv;  // q_i = z_i / r_ii
                 if (V == kNaive) {
                   pc = xv[q];  // p_i = A q_i from the second MV
                 } else {
                   pc = xv[q] * inv;  // p_i = x_i / r_ii (eq. (tec1))
-                  if (V == kHP) X[k + (int64_t)i * ldx] = pc;
+                  if (V == kHP) xcol(i)[k] = pc;
                 }
+                if (V != kHP && a.Pout) a.Pout[k + (int64_t)(i - kg) * a.ldpo] = pc;
               }
               s_pcur[r] = pc;
               s_qprev[r] = qv[q];
@@ -856,17 +883,21 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         __syncthreads();
         MGSA_TRACE(i, 4);
         if (ncols > 0)
-          fused_pass<V>(i, n, c0, crows, s_qprev, s_pprev, s_pcur, s_rrow, Q, ldq, X, ldx, s_piece, kmax, s_wfirst,
-                        s_wlast, s_racc);
+          fused_pass<V>(i, jbeg, ncols, kg, c0, crows, s_qprev, s_pprev, s_pcur, s_rrow, Q, ldq, X, ldx, s_piece,
+                        kmax, s_wfirst, s_wlast, s_racc);
       }
     }
     MGSA_TRACE(i, 6);
     if (ncols == 0) break;
-    for (int jr = tid; jr < ncols; jr += kThreads) part_cur[(int64_t)b * n + (i + 1 + jr)] = s_racc[jr];
+    for (int jr = tid; jr < ncols; jr += kThreads) part_cur[(int64_t)b * nt + (jbeg + jr)] = s_racc[jr];
     MGSA_TRACE(i, 7);
     if (!sync_all<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     MGSA_TRACE(i, 8);
-    reduce_first(part_cur, G, n, i, s_rrow, R, ldr, b == 0);  // r_{i,i+1}; the rest waits for the next barrier
+    if (given) {
+      reduce_rest(part_cur, G, nt, i, jbeg, s_rrow, s_buf, R, ldr, kg, b == 0);  // the whole row i
+    } else {
+      reduce_first(part_cur, G, nt, i, s_rrow, R, ldr, kg, b == 0);  // r_{i,i+1}; the rest at the next wait
+    }
     MGSA_TRACE(i, 9);
   }
   return 0;

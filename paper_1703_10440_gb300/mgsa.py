@@ -73,6 +73,8 @@ SIGNATURES = {
     "mgsa_qr_noalloc": (_INT, [ctypes.POINTER(mgsa_csr), _VP, _I64, _INT, _I64, _INT, _VP, _I64, _VP, _INT, _VP, _VP]),
     "mgsa_job_workspace_bytes": (_SZ, [_I64, _INT, _INT]),
     "mgsa_qr_batched": (_INT, [_VP, _INT, _VP, _VP, _VP]),
+    "mgsa_qr_append": (_INT, [_VP, ctypes.POINTER(mgsa_csr), _VP, _I64, _VP, _I64, _INT, _VP, _I64, _INT, _I64, _INT,
+                              _VP, _I64, _VP, _I64, _VP, _INT, _VP]),
     "mgsa_last_error": (ctypes.c_char_p, []),
 }
 MGSA_PARAM_MAX_CTAS, MGSA_PARAM_CHUNK_ROWS, MGSA_PARAM_MIN_ROWS_PER_CTA = 0, 1, 2
@@ -157,6 +159,14 @@ def mgsa_qr(h: int, A: mgsa_csr, Z, m: int, n: int, ldz: int, variant: int, Q, l
     """Queue one QR; returns the status (MGSA_OK or an argument error)."""
     return int(lib().mgsa_qr(h, ctypes.byref(A), _ptr(Z), m, n, ldz, variant, _ptr(Q), ldq, _ptr(R), ldr,
                              _stream(stream)))
+
+
+def mgsa_qr_append(h: int, A: mgsa_csr, Qold, ldqo: int, Pold, ldpo: int, k: int, Z, m: int, n: int, ldz: int,
+                   variant: int, Q, ldq: int, P, ldp: int, R, ldr: int, stream=None) -> int:
+    """Queue the orthogonalisation of Z against k given columns (Qold, Pold);
+    returns the status of the call.  ``P`` may be None."""
+    return int(lib().mgsa_qr_append(h, ctypes.byref(A), _ptr(Qold), ldqo, _ptr(Pold), ldpo, k, _ptr(Z), m, n, ldz,
+                                    variant, _ptr(Q), ldq, _ptr(P), ldp, _ptr(R), ldr, _stream(stream)))
 
 
 def mgsa_qr_noalloc(A: mgsa_csr, Z, m: int, n: int, ldz: int, variant: int, Q, ldq: int, R, ldr: int, info_dev=None,
@@ -249,6 +259,30 @@ class Handle:
         R = torch.empty((n, n), dtype=torch.float64, device=Z.device).T
         self.qr_into(A, Z, Q, R, variant, stream)
         return Q, R
+
+    def append(self, A, Qold, Pold, Z, variant, want_p: bool = True, stream=None):
+        """Orthonormalise the columns of ``Z`` against the given A-orthonormal
+        ``Qold`` (with ``Pold`` = its p_i; both None for none) and among
+        themselves.  Returns column-major ``(Q, P, R)``, R of shape (k+n, n);
+        P is None unless ``want_p``."""
+        import torch
+        rowptr, col, val = A
+        m, n = Z.shape
+        k = 0 if Qold is None else Qold.shape[1]
+        dev = Z.device
+        Q = torch.empty((n, m), dtype=torch.float64, device=dev).T
+        P = torch.empty((n, m), dtype=torch.float64, device=dev).T if want_p else None
+        R = torch.empty((n, k + n), dtype=torch.float64, device=dev).T
+        for t in [Z, Q, R] + ([P] if want_p else []) + ([Qold, Pold] if k else []):
+            if t.dtype.itemsize != 8 or t.stride(0) != 1:
+                raise ValueError("all matrices must be column-major float64 (stride(0) == 1)")
+        v = VARIANTS[variant] if isinstance(variant, str) else variant
+        csr = make_csr(m, col.numel(), rowptr, col, val)
+        st = mgsa_qr_append(self.h, csr, Qold, Qold.stride(1) if k else m, Pold, Pold.stride(1) if k else m, k, Z, m,
+                            n, Z.stride(1), v, Q, Q.stride(1), P, P.stride(1) if want_p else m, R, R.stride(1),
+                            stream)
+        _check(st)
+        return Q, P, R
 
     def set_param(self, param: int, value: int) -> None:
         mgsa_set_param(self.h, param, value)

@@ -9,6 +9,9 @@ Everything here is a thin ctypes wrapper around ``mgs_oracle.c``:
 
 * :func:`mgs` runs one of Algorithms 3-8 of the paper (naive / HA / HP, column-
   or row-oriented) in plain FP64 C and returns ``(Q, R, info, kind, mv_count)``.
+* :func:`cgs` runs the classical Gram-Schmidt counterparts (CGS-naive / HA /
+  HP, both forms), :func:`mgs_append` continues the column form after k given
+  A-orthonormal columns.
 * :func:`repr_error`, :func:`orth_loss` and :func:`chol_gram` evaluate the
   representation error ``||Z - QR||_F / ||Z||_F``, the loss of A-orthogonality
   ``||I - Q^T A Q||_F`` (both in double-double) and the long-double Cholesky
@@ -47,6 +50,8 @@ def _bind(lib):
     lib.oracle_mgs.restype = ctypes.c_int
     lib.oracle_mgs.argtypes = [i32, i32, i64, i32, ip, ip, dp, dp, i64, dp, i64, dp, i32,
                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_cgs.restype = ctypes.c_int
+    lib.oracle_cgs.argtypes = lib.oracle_mgs.argtypes
     lib.oracle_mgs_append.restype = ctypes.c_int
     lib.oracle_mgs_append.argtypes = [i32, i64, i32, i32, ip, ip, dp, dp, i64, dp, i64, dp, i64, dp, i64, dp, i64, dp,
                                       i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
@@ -98,6 +103,25 @@ def mgs(A, Z: np.ndarray, variant: str = "naive", form: str = "col", lib=None):
                           _ptr(Zf), m, _ptr(Q), m, _ptr(R), n, ctypes.byref(mv), ctypes.byref(kind))
     if info < 0:
         raise ValueError("oracle_mgs: invalid arguments")
+    return Q, R, int(info), int(kind.value), int(mv.value)
+
+
+def cgs(A, Z: np.ndarray, variant: str = "naive", form: str = "col", lib=None):
+    """Classical Gram-Schmidt counterpart of :func:`mgs` (Sections 2.3 and
+    3.3): the same algorithms with r_ij = p_i^T z_j^{(0)}.  Same arguments and
+    return value as :func:`mgs`."""
+    lib = lib or load()
+    rowptr, col, val = _csr_arrays(A)
+    Zf = _fortran(Z)
+    m, n = Zf.shape
+    Q = np.zeros((m, n), dtype=np.float64, order="F")
+    R = np.zeros((n, n), dtype=np.float64, order="F")
+    mv = ctypes.c_int64(0)
+    kind = ctypes.c_int(0)
+    info = lib.oracle_cgs(VARIANTS[variant], FORMS[form], m, n, _ptr(rowptr), _ptr(col), _ptr(val),
+                          _ptr(Zf), m, _ptr(Q), m, _ptr(R), n, ctypes.byref(mv), ctypes.byref(kind))
+    if info < 0:
+        raise ValueError("oracle_cgs: invalid arguments")
     return Q, R, int(info), int(kind.value), int(mv.value)
 
 

@@ -19,6 +19,10 @@
  *   Algorithm 7  MGS-HA(row)      n MV
  *   Algorithm 6  MGS-HP(col)      one block product X = AZ, x-recurrence (eq. (tec2))
  *   Algorithm 8  MGS-HP(row)      one block product X = AZ
+ * and the classical Gram-Schmidt counterparts CGS-naive / CGS-HA / CGS-HP in
+ * both forms (Section 2.3 and Section 3.3: the same recurrences with
+ * r_ij = p_i^T z_j^{(0)}, i.e. every coefficient of column j taken against the
+ * original column instead of the partly orthogonalised one).
  *
  * Arithmetic conventions (the paper fixes none of these):
  *   - IEEE binary64 throughout; the file is compiled with -ffp-contract=off,
@@ -51,6 +55,7 @@
  *   2  MGS-HP leaves x_j = A z_j^{(0)} (drops eq. (tec2)'s recurrence)
  *   3  the rank-1 update adds instead of subtracting
  *   4  r_ij uses the Euclidean inner product q_i^T z_j instead of p_i^T z_j
+ *   5  CGS takes r_ij against the working z_j^{(i-1)} (i.e. it becomes MGS)
  * The default build (ORACLE_MUTANT undefined or 0) has none of them. */
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0
@@ -401,6 +406,123 @@ int oracle_mgs_append(int variant, int64_t m, int k, int n, const int32_t* rowpt
   return info;
 }
 
+/* ---------------------------------------------------------------------- */
+/* CGS (Section 2.3; Section 3.3 states the recurrences): Algorithms 3/5/6 */
+/* and 4/7/8 with r_ij = p_i^T z_j^{(0)}.  Q's column j holds the working  */
+/* z_j^{(i)}; Z's column j keeps z_j^{(0)}.                                 */
+/* ---------------------------------------------------------------------- */
+
+/* r_ij of CGS: against the original column z0 (mutant 5: the working one). */
+static double cgs_coef(int64_t m, const double* p, const double* z0, const double* zwork) {
+#if ORACLE_MUTANT == 5
+  (void)z0;
+  return dot(m, p, zwork);
+#else
+  (void)zwork;
+  return dot(m, p, z0);
+#endif
+}
+
+/* Column form: for each j, r_ij (i < j) and z_j^{(i)} in ascending i, then
+ * x_j (naive / HA: one MV; HP: x_j^{(0)} - sum_i r_ij p_i), r_jj, q_j and p_j
+ * (naive: A q_j; HA / HP: x_j / r_jj, eq. (tec1)). */
+int oracle_cgs_col(int variant, int64_t m, int n, const int32_t* rowptr, const int32_t* col, const double* val,
+                   const double* Z, int64_t ldz, double* Q, int64_t ldq, double* R, int ldr, int64_t* mv_count,
+                   int* kind) {
+  double* P = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n); /* HP: x_j, then p_j */
+  double* x = (double*)malloc(sizeof(double) * (size_t)m);
+  int info = 0;
+  *kind = 0;
+  *mv_count = 0;
+  zero_R(n, R, ldr);
+  copy_cols(m, n, Z, ldz, Q, ldq);
+  if (variant == 2) {
+    for (int j = 0; j < n; ++j) csr_mv(m, rowptr, col, val, QC(j), P + (int64_t)j * m); /* X = A Z */
+    *mv_count = 1;
+  }
+  for (int j = 0; j < n && !info; ++j) {
+    double* zj = QC(j);
+    const double* z0 = Z + (int64_t)j * ldz;
+    for (int i = 0; i < j; ++i) {
+      RR(i, j) = cgs_coef(m, P + (int64_t)i * m, z0, zj); /* r_ij = p_i^T z_j^{(0)} */
+      axpy_sub(m, RR(i, j), QC(i), zj);                   /* z_j^{(i)} = z_j^{(i-1)} - r_ij q_i */
+    }
+    double* xj;
+    if (variant == 2) {
+      xj = P + (int64_t)j * m; /* x_j^{(j-1)} = x_j^{(0)} - sum_{i<j} r_ij p_i, ascending i */
+      for (int i = 0; i < j; ++i) axpy_sub(m, RR(i, j), P + (int64_t)i * m, xj);
+    } else {
+      csr_mv(m, rowptr, col, val, zj, x); /* x_j^{(j-1)} = A z_j^{(j-1)} */
+      ++*mv_count;
+      xj = x;
+    }
+    double s = dot(m, zj, xj);
+    if (!diag_ok(s, kind)) { info = j + 1; break; }
+    RR(j, j) = sqrt(s);
+    scale_div(m, zj, RR(j, j), zj); /* q_j */
+    if (variant == 0) {
+      csr_mv(m, rowptr, col, val, zj, P + (int64_t)j * m); /* p_j = A q_j */
+      ++*mv_count;
+    } else {
+      scale_div(m, xj, RR(j, j), P + (int64_t)j * m); /* p_j = x_j / r_jj */
+    }
+  }
+  free(P);
+  free(x);
+  return info;
+}
+
+/* Row form: at step i, q_i and p_i, then r_ij = p_i^T z_j^{(0)} and
+ * z_j^{(i)} (HP also x_j^{(i)}) for every j > i.  Same operations on every
+ * column as the column form, in the same order, hence the same results. */
+int oracle_cgs_row(int variant, int64_t m, int n, const int32_t* rowptr, const int32_t* col, const double* val,
+                   const double* Z, int64_t ldz, double* Q, int64_t ldq, double* R, int ldr, int64_t* mv_count,
+                   int* kind) {
+  double* X = (variant == 2) ? (double*)malloc(sizeof(double) * (size_t)m * (size_t)n) : NULL;
+  double* p = (double*)malloc(sizeof(double) * (size_t)m);
+  double* x = (double*)malloc(sizeof(double) * (size_t)m);
+  int info = 0;
+  *kind = 0;
+  *mv_count = 0;
+  zero_R(n, R, ldr);
+  copy_cols(m, n, Z, ldz, Q, ldq);
+  if (variant == 2) {
+    for (int j = 0; j < n; ++j) csr_mv(m, rowptr, col, val, QC(j), X + (int64_t)j * m);
+    *mv_count = 1;
+  }
+  for (int i = 0; i < n; ++i) {
+    double* zi = QC(i);
+    double* xi;
+    if (variant == 2) {
+      xi = X + (int64_t)i * m;
+    } else {
+      csr_mv(m, rowptr, col, val, zi, x); /* x_i^{(i-1)} = A z_i^{(i-1)} */
+      ++*mv_count;
+      xi = x;
+    }
+    double s = dot(m, zi, xi);
+    if (!diag_ok(s, kind)) { info = i + 1; break; }
+    RR(i, i) = sqrt(s);
+    scale_div(m, zi, RR(i, i), zi); /* q_i */
+    if (variant == 0) {
+      csr_mv(m, rowptr, col, val, zi, p); /* p_i = A q_i */
+      ++*mv_count;
+    } else {
+      scale_div(m, xi, RR(i, i), p); /* p_i = x_i / r_ii */
+    }
+    for (int j = i + 1; j < n; ++j) {
+      RR(i, j) = cgs_coef(m, p, Z + (int64_t)j * ldz, QC(j)); /* r_ij = p_i^T z_j^{(0)} */
+      axpy_sub(m, RR(i, j), zi, QC(j));
+    }
+    if (variant == 2)
+      for (int j = i + 1; j < n; ++j) axpy_sub(m, RR(i, j), p, X + (int64_t)j * m); /* x_j^{(i)} */
+  }
+  free(X);
+  free(p);
+  free(x);
+  return info;
+}
+
 /* Dispatcher: variant 0 = naive, 1 = HA, 2 = HP; form 0 = col, 1 = row. */
 int oracle_mgs(int variant, int form, int64_t m, int n, const int32_t* rowptr, const int32_t* col,
                const double* val, const double* Z, int64_t ldz, double* Q, int64_t ldq, double* R, int ldr,
@@ -415,6 +537,16 @@ int oracle_mgs(int variant, int form, int64_t m, int n, const int32_t* rowptr, c
     case 5: return oracle_mgs_hp_row(m, n, rowptr, col, val, Z, ldz, Q, ldq, R, ldr, mv_count, kind);
     default: return -1;
   }
+}
+
+/* CGS dispatcher, same conventions as oracle_mgs. */
+int oracle_cgs(int variant, int form, int64_t m, int n, const int32_t* rowptr, const int32_t* col,
+               const double* val, const double* Z, int64_t ldz, double* Q, int64_t ldq, double* R, int ldr,
+               int64_t* mv_count, int* kind) {
+  if (m < 1 || n < 1 || m < n || ldz < m || ldq < m || ldr < n) return -1;
+  if (variant < 0 || variant > 2 || form < 0 || form > 1) return -1;
+  return form == 0 ? oracle_cgs_col(variant, m, n, rowptr, col, val, Z, ldz, Q, ldq, R, ldr, mv_count, kind)
+                   : oracle_cgs_row(variant, m, n, rowptr, col, val, Z, ldz, Q, ldq, R, ldr, mv_count, kind);
 }
 
 /* y = A x in FP64, exported for tests of the generators. */

@@ -67,3 +67,38 @@ def test_planted_mistake_is_caught(k):
     if k in (3, 4):
         for v in MUTANTS[k]:
             assert not pins_pass(lib, v, claims=False), (k, v)
+
+
+def cgs_pins_pass(lib, variant) -> bool:
+    """The CGS pins of test_oracle_cgs.py: the Cholesky factor and the
+    quadratic growth of the loss with kappa(A^{1/2} Z) (Section 4.2)."""
+    A = W.banded_spd_csr(60, 3, W.rng(21, 400))
+    Z = np.asfortranarray(W.rng(21, 401).standard_normal((60, 8)))
+    Rc, _ = oracle.chol_gram(A, Z)
+    _, R, info, _, _ = oracle.cgs(A, Z, variant, "col", lib=lib)
+    if info != 0 or np.linalg.norm(R - Rc) / np.linalg.norm(Rc) > 1e-12:
+        return False
+    lzs = np.arange(2, 13) * 0.5
+    losses = []
+    for lz in lzs:
+        Ad, Z2, _ = W.exp2_problem(2.0, lz, 1)
+        A2 = W.dense_csr(Ad)
+        Q2, _, inf2, _, _ = oracle.cgs(A2, Z2, variant, "row", lib=lib)
+        if inf2 != 0:
+            return False
+        losses.append(oracle.orth_loss(A2, Q2))
+    slope = np.polyfit(lzs, np.log10(losses), 1)[0]
+    return 1.7 <= slope <= 2.3
+
+
+def test_unmutated_cgs_passes_its_pins():
+    for v in ("naive", "ha", "hp"):
+        assert cgs_pins_pass(oracle.load(), v)
+
+
+def test_cgs_turned_mgs_is_caught():
+    """Mutant 5 takes r_ij against the working column: the result is MGS,
+    exact in exact arithmetic, so only the loss growth can tell."""
+    lib = mutant_lib(5)
+    for v in ("naive", "ha", "hp"):
+        assert not cgs_pins_pass(lib, v), v

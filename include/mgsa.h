@@ -55,9 +55,16 @@ typedef struct CUstream_st* mgsa_stream_t;
 typedef struct mgsa_context* mgsa_handle;
 
 typedef enum {
-  MGSA_NAIVE = 0, /* Algorithm 4: 2n MV */
-  MGSA_HA = 1,    /* Algorithm 7: n MV, p_i = x_i / r_ii */
-  MGSA_HP = 2     /* Algorithm 8: X = AZ once, x-recurrence */
+  MGSA_NAIVE = 0,     /* Algorithm 4: 2n MV */
+  MGSA_HA = 1,        /* Algorithm 7: n MV, p_i = x_i / r_ii */
+  MGSA_HP = 2,        /* Algorithm 8: X = AZ once, x-recurrence */
+  /* Classical Gram-Schmidt counterparts (Section 2.3; recurrences in Section
+   * 3.3): r_ij = p_i^T z_j^{(0)}, run column by column (left-looking).  Their
+   * loss of A-orthogonality grows with kappa(A^{1/2} Z)^2 (Section 4.2), not
+   * linearly as for MGS.  mgsa_qr / mgsa_qr_host / mgsa_reserve only. */
+  MGSA_CGS_NAIVE = 3, /* 2n MV */
+  MGSA_CGS_HA = 4,    /* n MV, p_j = x_j / r_jj */
+  MGSA_CGS_HP = 5     /* X = AZ once, x-recurrence */
 } mgsa_variant;
 
 typedef enum {
@@ -103,7 +110,7 @@ mgsa_status mgsa_reserve(mgsa_handle h, int64_t m, int n, mgsa_variant v);
 size_t mgsa_workspace_bytes(mgsa_handle h, int64_t m, int n, mgsa_variant v);
 
 /* A-orthonormal thin QR of Z (Section 1, eq. (1)), right-looking MGS in the
- * form `v` (Algorithm 4, 7 or 8).
+ * form `v` (Algorithm 4, 7 or 8), or left-looking CGS (MGSA_CGS_*).
  *
  *   A      CSR matrix with A->m == m (device arrays, read only).
  *   Z      m x n input, column-major, leading dimension ldz >= m (read only).
@@ -169,8 +176,9 @@ mgsa_status mgsa_qr_host(mgsa_handle h, const int32_t* rowptr, const int32_t* co
  *               (Q, P) of one call as (Qold, Pold) of the next grows a basis.
  *   R           (k + n) x n output, leading dimension ldr >= k + n.
  *
- * Requirements: 0 <= k, 1 <= n, k + n <= MGSA_MAX_N, k + n <= m < 2^31; no
- * output overlaps an input or another output.  Status and info as for
+ * Requirements: v one of MGSA_NAIVE / MGSA_HA / MGSA_HP; 0 <= k, 1 <= n,
+ * k + n <= MGSA_MAX_N, k + n <= m < 2^31; no output overlaps an input or
+ * another output.  Status and info as for
  * mgsa_qr (info counts the columns of Z, 1-based).  mgsa_reserve(h, m, k + n,
  * v) makes the call allocation-free. */
 mgsa_status mgsa_qr_append(mgsa_handle h, const mgsa_csr* A, const double* Qold, int64_t ldqo, const double* Pold,

@@ -71,12 +71,33 @@ struct Plan {
   int xcols = 0;
   size_t x_bytes = 0;
   size_t part_bytes = 0;
+  int stages = 0;          // CGS: pivot buffers in shared memory
+  int64_t qp_doubles = 0;  // CGS: pivot blocks (inside x_bytes, after the X columns)
 };
 
 // nnz < 0: unknown (workspace sizing); long rows (warp-per-row MVs) carry
 // more work per row, so they get smaller slabs and thus more CTAs.  kg given
 // columns in front (successive orthogonalisation) widen the shared rows and
 // partial sums to kg + n columns; the X columns stay those of the n new ones.
+bool is_cgs(mgsa_variant v) { return v == MGSA_CGS_NAIVE || v == MGSA_CGS_HA || v == MGSA_CGS_HP; }
+
+// Kernel template index (naive / HA / HP) of a public variant.
+int kernel_variant(mgsa_variant v) { return is_cgs(v) ? (int)v - 3 : (int)v; }
+
+constexpr int kCgsStagedChunk = 2048;  // CGS slabs above one chunk: rows per streamed chunk
+
+// Shared memory of a plan (and, for CGS, the number of pivot buffers).
+mgsa_status plan_smem(mgsa_variant v, int nt, int chunk, size_t* smem, int* stages) {
+  *stages = 0;
+  if (!is_cgs(v)) {
+    *smem = mgsa::sweep_smem_bytes(nt, chunk);
+    return MGSA_OK;
+  }
+  cudaError_t e = mgsa::cgs_smem_plan(kernel_variant(v), nt, chunk, stages, smem);
+  if (e == cudaErrorInvalidValue) return fail(MGSA_ERR_INVALID, "n too large for the CGS kernel's shared memory");
+  return e == cudaSuccess ? MGSA_OK : cuda_fail(e);
+}
+
 mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, Plan* p, int64_t nnz = -1,
                       int kg = 0) {
   const int nt = kg + n;
@@ -84,7 +105,12 @@ mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, P
   const bool long_rows = nnz >= (int64_t)mgsa::kWarpRowNnz * m;
   const int64_t min_rows = h->min_rows > 0 ? h->min_rows : (long_rows ? mgsa::kMinRowsLongRows : mgsa::kMinRowsPerCta);
   int max_ctas = 0;
-  cudaError_t e = mgsa::sweep_max_ctas((int)v, mgsa::sweep_smem_bytes(nt, chunk_cap), &max_ctas);
+  const int kv = kernel_variant(v);
+  size_t smem_cap = 0;
+  int stages = 0;
+  mgsa_status st = plan_smem(v, nt, chunk_cap, &smem_cap, &stages);
+  if (st != MGSA_OK) return st;
+  cudaError_t e = is_cgs(v) ? mgsa::cgs_max_ctas(kv, smem_cap, &max_ctas) : mgsa::sweep_max_ctas(kv, smem_cap, &max_ctas);
   if (e != cudaSuccess) return cuda_fail(e);
   if (max_ctas < 1) return fail(MGSA_ERR_CUDA, "sweep kernel does not fit on this device");
   int64_t g = std::min<int64_t>(max_ctas, (m + min_rows - 1) / min_rows);
@@ -93,12 +119,20 @@ mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, P
   p->rpc = round_up((m + g - 1) / g, 32);
   p->grid = (int)((m + p->rpc - 1) / p->rpc);
   p->chunk = (int)std::min<int64_t>(chunk_cap, p->rpc);
-  p->smem = mgsa::sweep_smem_bytes(nt, p->chunk);
+  // CGS streams a slab that is not one chunk in smaller chunks, so that more
+  // pivot buffers fit in shared memory.
+  if (is_cgs(v) && p->rpc > chunk_cap && h->chunk_rows == 0) p->chunk = kCgsStagedChunk;
+  if ((st = plan_smem(v, nt, p->chunk, &p->smem, &p->stages)) != MGSA_OK) return st;
   p->ldx = round_up(m, 32);
-  p->xcols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
-  p->x_bytes = (size_t)round_up((int64_t)sizeof(double) * p->ldx * p->xcols, 256);
+  if (is_cgs(v)) p->xcols = v == MGSA_CGS_HP ? n : 2;
+  else p->xcols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
+  // CGS pivot blocks: 2 * n * G * rpc doubles, and G * rpc <= m + 32 * G for
+  // every grid G a plan can choose, so a reservation fits every nnz.
+  const int64_t gmax = std::max<int64_t>(max_ctas, p->grid);
+  p->qp_doubles = is_cgs(v) ? 2 * (int64_t)n * (p->ldx + 32 * gmax) : 0;
+  p->x_bytes = (size_t)round_up((int64_t)sizeof(double) * (p->ldx * p->xcols + p->qp_doubles), 256);
   // Partials for the largest grid any plan can use, so a reservation fits every nnz.
-  p->part_bytes = sizeof(double) * (size_t)(2 * nt + 1) * (size_t)std::max<int64_t>(max_ctas, p->grid);
+  p->part_bytes = sizeof(double) * (size_t)(2 * nt + 1) * (size_t)gmax;
   return MGSA_OK;
 }
 
@@ -126,7 +160,7 @@ mgsa_status check_sizes(int64_t m, int n, int64_t ldz, mgsa_variant v, int64_t l
   if (m < n || m >= ((int64_t)1 << 31)) return fail(MGSA_ERR_INVALID, "m must satisfy n <= m < 2^31");
   if (ldz < m || ldq < m) return fail(MGSA_ERR_INVALID, "leading dimension of Z or Q below m");
   if (ldr < n) return fail(MGSA_ERR_INVALID, "leading dimension of R below n");
-  if (v != MGSA_NAIVE && v != MGSA_HA && v != MGSA_HP) return fail(MGSA_ERR_INVALID, "unknown variant");
+  if ((int)v < (int)MGSA_NAIVE || (int)v > (int)MGSA_CGS_HP) return fail(MGSA_ERR_INVALID, "unknown variant");
   return MGSA_OK;
 }
 
@@ -152,7 +186,8 @@ mgsa_status mgsa_create(mgsa_handle* h, int device) {
   if (!c) return fail(MGSA_ERR_NOMEM, "host allocation failed");
   c->device = device;
   if ((e = cudaMalloc(&c->ctl, 256)) != cudaSuccess || (e = cudaMemset(c->ctl, 0, 256)) != cudaSuccess ||
-      (e = cudaMallocHost(&c->ctl_host, 256)) != cudaSuccess || (e = mgsa::sweep_prepare(device)) != cudaSuccess) {
+      (e = cudaMallocHost(&c->ctl_host, 256)) != cudaSuccess || (e = mgsa::sweep_prepare(device)) != cudaSuccess ||
+      (e = mgsa::cgs_prepare(device)) != cudaSuccess) {
     mgsa_status s = cuda_fail(e);
     mgsa_destroy(c);
     return s;
@@ -230,6 +265,7 @@ static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, 
   if (kg < 0 || kg > MGSA_MAX_N - 1) return fail(MGSA_ERR_INVALID, "k must be in [0, MGSA_MAX_N)");
   mgsa_status st = check_sizes(m, n, ldz, v, ldq, n);  // ldr is checked against k + n below
   if (st != MGSA_OK) return st;
+  if (is_cgs(v) && (kg > 0 || P)) return fail(MGSA_ERR_INVALID, "the CGS variants take no given columns and no P");
   const int nt = kg + n;
   if (nt > MGSA_MAX_N) return fail(MGSA_ERR_INVALID, "k + n must be <= MGSA_MAX_N");
   if (m < nt) return fail(MGSA_ERR_INVALID, "m must be >= k + n");
@@ -286,6 +322,10 @@ static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, 
   a.rpc = p.rpc;
   a.chunk = p.chunk;
   a.mv_warp = A->nnz >= (int64_t)mgsa::kWarpRowNnz * m;
+  if (is_cgs(v)) {
+    a.qp = a.X + p.ldx * p.xcols;
+    a.stages = p.stages;
+  }
   a.kg = kg;
   a.Qg = Qg;
   a.ldqg = ldqg;
@@ -302,7 +342,8 @@ static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, 
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
   cudaError_t e = cudaMemsetAsync(h->ctl, 0, sizeof(int) * mgsa::kCtlWords, cs);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = mgsa::sweep_launch((int)v, a, p.grid, p.smem, cs);
+  e = is_cgs(v) ? mgsa::cgs_launch(kernel_variant(v), a, p.grid, p.smem, cs)
+                : mgsa::sweep_launch(kernel_variant(v), a, p.grid, p.smem, cs);
   if (e != cudaSuccess) return cuda_fail(e);
   return MGSA_OK;
 }
@@ -315,6 +356,7 @@ mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m
 mgsa_status mgsa_qr_append(mgsa_handle h, const mgsa_csr* A, const double* Qold, int64_t ldqo, const double* Pold,
                            int64_t ldpo, int k, const double* Z, int64_t m, int n, int64_t ldz, mgsa_variant v,
                            double* Q, int64_t ldq, double* P, int64_t ldp, double* R, int ldr, mgsa_stream_t s) {
+  if (is_cgs(v)) return fail(MGSA_ERR_INVALID, "mgsa_qr_append takes the MGS variants only");
   return qr_launch(h, A, Z, m, n, ldz, v, Q, ldq, R, ldr, k, Qold, ldqo, Pold, ldpo, P, ldp, s);
 }
 

@@ -51,6 +51,11 @@ struct SweepArgs {
   int64_t ldpg = 0;
   double* Pout = nullptr;  // optional p_j of the new columns (HA / naive; HP keeps them in X)
   int64_t ldpo = 0;
+  // CGS only: q_j and p_j per CTA slab, block (j, b) = [q rows | p rows] of
+  // rpc doubles each at qp + (j*G + b) * 2 * rpc; `stages` shared-memory
+  // buffers of 2 * chunk doubles feed them to the update pass.
+  double* qp = nullptr;
+  int stages = 0;
 };
 
 // Average row length from which a warp, not a thread, takes one CSR row.
@@ -99,6 +104,15 @@ void set_last_error(const char* why);
 cudaError_t sweep_prepare(int device);  // sets shared-memory attributes once per device
 cudaError_t sweep_max_ctas(int variant, size_t smem, int* max_ctas);
 cudaError_t sweep_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s);
+
+// Left-looking CGS kernels (mgsa_cgs.cu); variant = kNaive / kHA / kHP.
+// X holds n columns (HP: x_j) or 2 (HA, naive: z_j, x_j); qp as in SweepArgs.
+// cgs_smem_plan picks the number of pivot buffers that fit next to the rest.
+constexpr int kCgsMaxStages = 8;
+cudaError_t cgs_smem_plan(int variant, int n, int chunk, int* stages, size_t* smem);
+cudaError_t cgs_prepare(int device);
+cudaError_t cgs_max_ctas(int variant, size_t smem, int* max_ctas);
+cudaError_t cgs_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t batch_prepare(int device, size_t smem);
 cudaError_t batch_max_ctas(size_t smem, int* max_ctas);
 cudaError_t batch_launch(const BatchArgs& ba, int grid, size_t smem, cudaStream_t s);

@@ -73,7 +73,7 @@ extern "C" mgsa_status mgsa_qr_noalloc(const mgsa_csr* A, const double* Z, int64
   if (n < 1 || n > MGSA_MAX_N) return fail(MGSA_ERR_INVALID, "n must be in [1, MGSA_MAX_N]");
   if (m < n || m >= ((int64_t)1 << 31)) return fail(MGSA_ERR_INVALID, "m must satisfy n <= m < 2^31");
   if (ldz < m || ldq < m || ldr < n) return fail(MGSA_ERR_INVALID, "leading dimension too small");
-  if (v != MGSA_NAIVE && v != MGSA_HA && v != MGSA_HP) return fail(MGSA_ERR_INVALID, "unknown variant");
+  if (v != MGSA_NAIVE && v != MGSA_HA && v != MGSA_HP) return fail(MGSA_ERR_INVALID, "unknown or CGS variant");
   if (A->m != m) return fail(MGSA_ERR_INVALID, "A->m differs from m");
   if (A->nnz < 0 || A->nnz >= ((int64_t)1 << 31)) return fail(MGSA_ERR_INVALID, "nnz must be in [0, 2^31)");
   if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return fail(MGSA_ERR_INVALID, "NULL CSR array");

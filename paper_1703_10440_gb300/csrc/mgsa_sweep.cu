@@ -30,7 +30,7 @@
 // fixed orders that do not depend on timing; every CTA sums the G per-CTA
 // partials in the same order.  Device-wide waits are bounded (kSpinLimitNs);
 // on timeout the status word is set and every CTA returns.
-#include "mgsa_internal.cuh"
+#include "mgsa_device.cuh"
 
 // Phase tracing (off unless compiled with -DMGSA_PHASE_TRACE): CTA 0 records
 // %globaltimer at the phase boundaries of every step into g_mgsa_trace, which
@@ -57,174 +57,6 @@ namespace mgsa {
 
 namespace {
 
-__device__ __forceinline__ unsigned long long global_timer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Plain loads that bypass L1: data written by other CTAs during this kernel.
-__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
-
-__device__ __forceinline__ double warp_sum(double v) {
-  // Butterfly: every lane ends with the same value (each pairwise sum is the
-  // same two operands in every lane, and + is commutative).
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Deterministic CTA-wide sum returned to every thread: the 512 values go to
-// shared memory, lane l of warp 0 adds values l, l+32, ... in order, then a
-// butterfly.  (21 warp-wide FP64 instructions instead of 85 for 16 butterflies.)
-__device__ double block_sum(double v, double* s_buf) {
-  s_buf[threadIdx.x] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = s_buf[threadIdx.x];
-#pragma unroll
-    for (int w = 1; w < kWarps; ++w) t += s_buf[threadIdx.x + 32 * w];
-    t = warp_sum(t);
-    if (threadIdx.x == 0) s_buf[kThreads] = t;
-  }
-  __syncthreads();
-  const double r = s_buf[kThreads];
-  __syncthreads();
-  return r;
-}
-
-__device__ void set_status(int* ctl, int code, int column) {
-  if (atomicCAS(&ctl[kCtlStatus], 0, code) == 0) atomicExch(&ctl[kCtlColumn], column);
-}
-
-// Device-wide barrier for a cooperative launch, in two halves so that a CTA
-// can do independent work between arriving and waiting.  The counter only
-// grows during a launch (it is zeroed before each launch): barrier number k
-// (k = 1, 2, ...) is passed once it reaches k * gridDim.x.  Arrival is a
-// fire-and-forget release reduction; every CTA then polls the counter with
-// acquire loads.  Only thread 0 of a CTA touches it; `gen` (the number of
-// barriers passed) is meaningful in thread 0 only.
-__device__ __forceinline__ void grid_arrive(int* ctl, unsigned int gen, int* s_unused) {
-  (void)gen;
-  (void)s_unused;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int* count = reinterpret_cast<unsigned int*>(&ctl[kCtlBarCount]);
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
-  }
-}
-
-// Returns false if the wait ran past kSpinLimitNs or another CTA already
-// recorded a failure (then every CTA leaves the kernel).
-__device__ bool grid_wait(int* ctl, unsigned int& gen, const int* s_unused, int* s_ok) {
-  (void)s_unused;
-  if (threadIdx.x == 0) {
-    const unsigned int* count = reinterpret_cast<const unsigned int*>(&ctl[kCtlBarCount]);
-    const unsigned int target = (gen + 1u) * gridDim.x;
-    int ok = 1;
-    if (ld_acquire_u32(count) < target) {
-      const unsigned long long t0 = global_timer_ns();
-      unsigned int polls = 0;
-      while (ld_acquire_u32(count) < target) {
-        if ((++polls & 255u) == 0u) {
-          if (ld_relaxed_i32(&ctl[kCtlStatus]) != 0) { ok = 0; break; }
-          if (global_timer_ns() - t0 > kSpinLimitNs) {
-            set_status(ctl, kDevTimeout, -1);
-            ok = 0;
-            break;
-          }
-        }
-      }
-    }
-    gen += 1u;
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
-}
-
-__device__ __forceinline__ bool grid_sync(int* ctl, unsigned int& gen, int* s_flags) {
-  grid_arrive(ctl, gen, s_flags);
-  return grid_wait(ctl, gen, s_flags, s_flags + 1);
-}
-
-// Synchronisation of the step body: device-wide for the single-instance
-// kernel, CTA-wide when one CTA owns a whole instance (batched kernel).
-template <bool kBatch>
-__device__ __forceinline__ void sync_arrive(int* ctl, unsigned int gen, int* s_flags) {
-  if (kBatch) __syncthreads();
-  else grid_arrive(ctl, gen, s_flags);
-}
-
-template <bool kBatch>
-__device__ __forceinline__ bool sync_wait(int* ctl, unsigned int& gen, int* s_flags) {
-  if (kBatch) {
-    __syncthreads();
-    return true;
-  }
-  return grid_wait(ctl, gen, s_flags, s_flags + 1);
-}
-
-template <bool kBatch>
-__device__ __forceinline__ bool sync_all(int* ctl, unsigned int& gen, int* s_flags) {
-  sync_arrive<kBatch>(ctl, gen, s_flags);
-  return sync_wait<kBatch>(ctl, gen, s_flags);
-}
-
-// Result of the step body: 0, or (device status << 24) | 1-based column.
-__device__ __forceinline__ int body_result(int status, int column) { return (status << 24) | (column & 0xFFFFFF); }
-
-// Sum over CTAs b (in order of b, fixed tree) of part[b * stride], by warp 0;
-// lane 0 returns the sum.
-__device__ __forceinline__ double warp0_sum_ctas(const double* part, int64_t stride, int G) {
-  double t = 0.0;
-  for (int b0 = 0; b0 < G; b0 += 160) {
-    double v[5];
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-      const int bb = b0 + (int)threadIdx.x + 32 * s;
-      v[s] = bb < G ? ld_cg(part + bb * stride) : 0.0;
-    }
-    t += (((v[0] + v[1]) + v[2]) + v[3]) + v[4];
-  }
-  return warp_sum(t);
-}
-
-// r_ii from the norm partials: one thread forms the sum's square root, its
-// reciprocal and the breakdown verdict and broadcasts them.
-// s_scal[0] = r_ii, s_scal[1] = 1/r_ii, s_scal[2] = status (0 ok).
-__device__ void diagonal(const double* part_norm, int G, double* s_scal) {
-  if (threadIdx.x < 32) {
-    const double stot = warp0_sum_ctas(part_norm, 1, G);
-    if (threadIdx.x == 0) {
-      int st = kDevOk;
-      double r = 0.0, inv = 0.0;
-      if (isnan(stot) || isinf(stot)) st = kDevNonfinite;
-      else if (!(stot > 0.0)) st = kDevBreakdown;
-      else {
-        r = sqrt(stot);
-        inv = 1.0 / r;
-      }
-      s_scal[0] = r;
-      s_scal[1] = inv;
-      s_scal[2] = (double)st;
-    }
-  }
-  __syncthreads();
-}
-
 // r_{i,i+1}: the first entry of row i right of the diagonal (warp 0).  Column
 // j of the virtual matrix is column j - kg of R.
 __device__ void reduce_first(const double* part, int G, int nt, int i, double* s_rrow, double* R, int ldr, int kg,
@@ -239,88 +71,7 @@ __device__ void reduce_first(const double* part, int G, int nt, int i, double* s
   __syncthreads();
 }
 
-// r_ij for j = jstart .. nt-1, lane per column: warp w adds the partials of
-// the CTAs in [w*G/16, (w+1)*G/16) in order, then warp 0 adds the 16 warp sums
-// in order.  Loads are coalesced because part is laid out [CTA][column].
-__device__ void reduce_rest(const double* part, int G, int nt, int i, int jstart, double* s_rrow, double* s_buf,
-                            double* R, int ldr, int kg, bool write_r) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int bb0 = (int)((int64_t)G * warp / kWarps), bb1 = (int)((int64_t)G * (warp + 1) / kWarps);
-  for (int j0 = jstart; j0 < nt; j0 += 32) {
-    const int j = j0 + lane;
-    double t0 = 0.0, t1 = 0.0;
-    int bb = bb0;
-    for (; bb + 1 < bb1; bb += 2) {
-      const double v0 = j < nt ? ld_cg(part + (int64_t)bb * nt + j) : 0.0;
-      const double v1 = j < nt ? ld_cg(part + (int64_t)(bb + 1) * nt + j) : 0.0;
-      t0 += v0;
-      t1 += v1;
-    }
-    if (bb < bb1) t0 += j < nt ? ld_cg(part + (int64_t)bb * nt + j) : 0.0;
-    s_buf[threadIdx.x] = t0 + t1;
-    __syncthreads();
-    if (warp == 0 && j < nt) {
-      double t = s_buf[lane];
-#pragma unroll
-      for (int w = 1; w < kWarps; ++w) t += s_buf[lane + 32 * w];
-      s_rrow[j] = t;
-      if (write_r) R[i + (int64_t)(j - kg) * ldr] = t;
-    }
-    __syncthreads();
-  }
-}
-
 constexpr int kTripRows = 8;                     // rows per lane per trip of the fused pass
-constexpr int kResRows = kMaxChunk / kThreads;  // rows per thread when a CTA's slab is one chunk
-
-// out[q] = sum_e val[e] * (scale_src ? src[col[e]] * scale : src[col[e]]) for
-// the rows k + q*kThreads (q < 4) below k1, each summed in stored order.  The
-// four rows advance in lockstep so their gathers are in flight together.
-__device__ __forceinline__ void csr_rows4(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                          const double* __restrict__ val, const double* src, double scale,
-                                          bool scale_src, int64_t k, int64_t k1, double out[4]) {
-  int e[4], e1[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t kk = k + q * kThreads;
-    e[q] = kk < k1 ? __ldg(rowptr + kk) : 0;
-    e1[q] = kk < k1 ? __ldg(rowptr + kk + 1) : 0;
-    out[q] = 0.0;
-  }
-  while (e[0] < e1[0] || e[1] < e1[1] || e[2] < e1[2] || e[3] < e1[3]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (e[q] < e1[q]) {
-        const double zv = ld_cg(src + __ldg(colidx + e[q]));
-        out[q] = fma(__ldg(val + e[q]), scale_src ? zv * scale : zv, out[q]);
-        ++e[q];
-      }
-    }
-  }
-}
-
-// Long rows: one warp per row.  Lane l takes the entries e0 + l, e0 + l + 32,
-// ... (coalesced column and value loads), two accumulators, then a butterfly;
-// every lane returns the row's sum (a fixed tree, so deterministic).
-__device__ __forceinline__ double csr_row_warp(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                               const double* __restrict__ val, const double* src, double scale,
-                                               bool scale_src, int64_t k) {
-  const int lane = threadIdx.x & 31;
-  const int e0 = __ldg(rowptr + k), e1 = __ldg(rowptr + k + 1);
-  double acc0 = 0.0, acc1 = 0.0;
-  int e = e0 + lane;
-  for (; e + 32 < e1; e += 64) {
-    const double g0 = ld_cg(src + __ldg(colidx + e));
-    const double g1 = ld_cg(src + __ldg(colidx + e + 32));
-    acc0 = fma(__ldg(val + e), scale_src ? g0 * scale : g0, acc0);
-    acc1 = fma(__ldg(val + e + 32), scale_src ? g1 * scale : g1, acc1);
-  }
-  if (e < e1) {
-    const double g0 = ld_cg(src + __ldg(colidx + e));
-    acc0 = fma(__ldg(val + e), scale_src ? g0 * scale : g0, acc0);
-  }
-  return warp_sum(acc0 + acc1);
-}
 
 // The fused pass over one chunk of rows [c0, c0 + crows) and the columns
 // j = jbeg .. jbeg+ncols-1: apply step i-1's updates z_j -= r_{i-1,j} q_{i-1} (HP:
@@ -448,100 +199,11 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
   if (b == 0) {
     for (int64_t t = tid; t < (int64_t)nt * n; t += kThreads) R[(t % nt) + (t / nt) * ldr] = 0.0;
   }
-  if (V == kHP && a.mv_warp) {
-    // X = A Z with one warp per (long) row, kPanel columns at a time: lanes
-    // split the row's entries, one butterfly per column.
-    constexpr int kPanel = 8;
-    const int lane = tid & 31, warp = tid >> 5;
-    double s0 = 0.0;
-    for (int64_t k = k0 + warp; k < k1; k += kWarps) {
-      const int e0 = __ldg(rowptr + k), e1 = __ldg(rowptr + k + 1);
-      for (int j0 = 0; j0 < n; j0 += kPanel) {
-        const int w = (n - j0) < kPanel ? (n - j0) : kPanel;
-        double acc[kPanel];
-#pragma unroll
-        for (int jj = 0; jj < kPanel; ++jj) acc[jj] = 0.0;
-        for (int e = e0 + lane; e < e1; e += 32) {
-          const double v = __ldg(val + e);
-          const double* zc = Z + __ldg(colidx + e) + (int64_t)j0 * ldz;
-#pragma unroll
-          for (int jj = 0; jj < kPanel; ++jj)
-            if (jj < w) acc[jj] = fma(v, __ldg(zc + jj * ldz), acc[jj]);
-        }
-#pragma unroll
-        for (int jj = 0; jj < kPanel; ++jj) {
-          if (jj < w) {
-            const double x = warp_sum(acc[jj]);
-            if (lane == jj) {
-              const double zk = __ldg(Z + k + (int64_t)(j0 + jj) * ldz);
-              X[k + (int64_t)(j0 + jj) * ldx] = x;
-              Q[k + (int64_t)(j0 + jj) * ldq] = zk;
-              if (j0 + jj == 0) s0 = fma(zk, x, s0);
-            }
-          }
-        }
-      }
-    }
+  if (V == kHP) {
+    const double s0 = spmm_slab(rowptr, colidx, val, Z, ldz, X, ldx, Q, ldq, k0, k1, n, a.mv_warp != 0);
     if (!resident) {
-      s0 = block_sum(s0, s_buf);
-      if (tid == 0) part_norm[b] = s0;
-    }
-  } else if (V == kHP) {
-    // X = A Z: four rows per thread in lockstep, kPanel columns at a time, so
-    // the gathers of four rows are in flight together.
-    constexpr int kPanel = 8;
-    double s0 = 0.0;
-    for (int64_t kb = k0 + tid; kb < k1; kb += 4 * kThreads) {
-      int eb[4], ee[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t kk = kb + q * kThreads;
-        eb[q] = kk < k1 ? __ldg(rowptr + kk) : 0;
-        ee[q] = kk < k1 ? __ldg(rowptr + kk + 1) : 0;
-      }
-      for (int j0 = 0; j0 < n; j0 += kPanel) {
-        const int w = (n - j0) < kPanel ? (n - j0) : kPanel;
-        double acc[4][kPanel];
-        int e[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          e[q] = eb[q];
-#pragma unroll
-          for (int jj = 0; jj < kPanel; ++jj) acc[q][jj] = 0.0;
-        }
-        while (e[0] < ee[0] || e[1] < ee[1] || e[2] < ee[2] || e[3] < ee[3]) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (e[q] < ee[q]) {
-              const double v = __ldg(val + e[q]);
-              const double* zc = Z + __ldg(colidx + e[q]) + (int64_t)j0 * ldz;
-#pragma unroll
-              for (int jj = 0; jj < kPanel; ++jj)
-                if (jj < w) acc[q][jj] = fma(v, __ldg(zc + jj * ldz), acc[q][jj]);
-              ++e[q];
-            }
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int64_t kk = kb + q * kThreads;
-          if (kk < k1) {
-#pragma unroll
-            for (int jj = 0; jj < kPanel; ++jj) {
-              if (jj < w) {
-                const double zk = __ldg(Z + kk + (int64_t)(j0 + jj) * ldz);
-                X[kk + (int64_t)(j0 + jj) * ldx] = acc[q][jj];
-                Q[kk + (int64_t)(j0 + jj) * ldq] = zk;
-                if (j0 + jj == 0) s0 = fma(zk, acc[q][0], s0);
-              }
-            }
-          }
-        }
-      }
-    }
-    if (!resident) {
-      s0 = block_sum(s0, s_buf);
-      if (tid == 0) part_norm[b] = s0;
+      const double t = block_sum(s0, s_buf);
+      if (tid == 0) part_norm[b] = t;
     }
   } else {
     for (int j = 0; j < n; ++j)
@@ -626,7 +288,8 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       }
       MGSA_TRACE(i, 1);
       sync_arrive<kBatch>(a.ctl, gen, s_flags);
-      if (rest_prev) reduce_rest(part_prev, G, nt, i - 1, i + 1, s_rrow, s_buf, R, ldr, kg, b == 0);  // r_{i-1,j>i}
+      if (rest_prev)  // r_{i-1,j}, j > i
+        reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
       if (!sync_wait<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     } else {
       const double* zsrc;  // column i of the working Z, complete on every row
@@ -665,7 +328,8 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
           }
         }
         sync_arrive<kBatch>(a.ctl, gen, s_flags);
-        if (rest_prev) reduce_rest(part_prev, G, nt, i - 1, i + 1, s_rrow, s_buf, R, ldr, kg, b == 0);
+        if (rest_prev)
+          reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
         if (!sync_wait<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
         zsrc = zi;
       } else {
@@ -894,7 +558,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     if (!sync_all<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     MGSA_TRACE(i, 8);
     if (given) {
-      reduce_rest(part_cur, G, nt, i, jbeg, s_rrow, s_buf, R, ldr, kg, b == 0);  // the whole row i
+      reduce_range(part_cur, G, nt, jbeg, nt, s_rrow, s_buf, b == 0 ? R + i : nullptr, ldr, kg);  // all of row i
     } else {
       reduce_first(part_cur, G, nt, i, s_rrow, R, ldr, kg, b == 0);  // r_{i,i+1}; the rest at the next wait
     }

@@ -17,7 +17,9 @@ import threading
 from . import build as _build
 
 MGSA_NAIVE, MGSA_HA, MGSA_HP = 0, 1, 2
-VARIANTS = {"naive": MGSA_NAIVE, "ha": MGSA_HA, "hp": MGSA_HP}
+MGSA_CGS_NAIVE, MGSA_CGS_HA, MGSA_CGS_HP = 3, 4, 5
+VARIANTS = {"naive": MGSA_NAIVE, "ha": MGSA_HA, "hp": MGSA_HP,
+            "cgs_naive": MGSA_CGS_NAIVE, "cgs_ha": MGSA_CGS_HA, "cgs_hp": MGSA_CGS_HP}
 
 MGSA_OK = 0
 MGSA_ERR_INVALID = 1

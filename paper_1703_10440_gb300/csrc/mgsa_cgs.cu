@@ -40,6 +40,26 @@
 // gather, column 1 x_j (staged mode).
 #include "mgsa_device.cuh"
 
+// Phase tracing (off unless compiled with -DMGSA_PHASE_TRACE): CTA 0 records
+// %globaltimer at the phase boundaries of every column into g_cgs_trace,
+// exported by the traced build through mgsa_cgs_trace_fetch.
+#ifdef MGSA_PHASE_TRACE
+__device__ unsigned long long g_cgs_trace[4200][12];
+extern "C" int mgsa_cgs_trace_fetch(unsigned long long* host) {
+  return (int)cudaMemcpyFromSymbol(host, g_cgs_trace, sizeof(g_cgs_trace));
+}
+#define CGS_TRACE(col, slot)                                              \
+  do {                                                                    \
+    if (blockIdx.x == 0 && threadIdx.x == 0) {                            \
+      unsigned long long t_;                                              \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));              \
+      g_cgs_trace[(col)][(slot)] = t_;                                    \
+    }                                                                     \
+  } while (0)
+#else
+#define CGS_TRACE(col, slot) ((void)0)
+#endif
+
 namespace mgsa {
 
 namespace {
@@ -417,6 +437,7 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
     const double* z1col = has_next ? Z + (int64_t)(j + 1) * ldz : nullptr;
 
     // ---------------- U: z_j (HP: x_j) and the next column's dots ----------------
+    CGS_TRACE(j, 0);
     double sl = 0.0;
     if (resident) {
       if (V == kHP) load_slots(X + (int64_t)j * ldx, k0, crows_all, xr);
@@ -463,22 +484,27 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
     }
 
     // ---------------- MV (HA, naive) and the diagonal ----------------
+    CGS_TRACE(j, 1);
     if (V == kHP) {
       sl = block_sum(sl, s_buf);
       if (tid == 0) part_norm[b] = sl;
       if (!sync_all<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     } else {
       if (!sync_all<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);  // z_j complete in W
+      CGS_TRACE(j, 2);
       sl = mv_rows(rowptr, colidx, val, W, 1.0, false, k0, k1, resident, warp_rows, xr, zr, XS, s_xtmp, true);
       sl = block_sum(sl, s_buf);
       if (tid == 0) part_norm[b] = sl;
+      CGS_TRACE(j, 3);
       sync_arrive<false>(a.ctl, gen, s_flags);
       // r_{i,j+1}, i < j: their partials were stored before the previous wait.
       if (has_next && j > 0)
         reduce_range(part_cur, G, n, 0, j, s_rnext, s_buf, b == 0 ? R + (int64_t)(j + 1) * ldr : nullptr, 1, 0);
       if (!sync_wait<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     }
+    CGS_TRACE(j, 4);
     diagonal(part_norm, G, s_scal);
+    CGS_TRACE(j, 5);
     if (s_scal[2] != 0.0) return body_result((int)s_scal[2], j + 1);  // the same verdict in every CTA
     const double inv = s_scal[1];
     if (b == 0 && tid == 0) R[j + (int64_t)j * ldr] = s_scal[0];
@@ -521,15 +547,18 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
       }
     }
     fence_proxy_async_global();  // the block of pivot j is read by bulk copies from the next column on
+    CGS_TRACE(j, 6);
     if (!has_next) break;
     dj = block_sum(dj, s_buf);
     if (tid == 0) part_cur[(int64_t)b * n + j] = dj;
+    CGS_TRACE(j, 7);
 
     // ---------------- r_{:,j+1} ----------------
     sync_arrive<false>(a.ctl, gen, s_flags);
     if (V == kHP && j > 0)
       reduce_range(part_cur, G, n, 0, j, s_rnext, s_buf, b == 0 ? R + (int64_t)(j + 1) * ldr : nullptr, 1, 0);
     if (!sync_wait<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+    CGS_TRACE(j, 8);
     if (tid < 32) {
       const double r = warp0_sum_ctas(part_cur + j, n, G);
       if (tid == 0) {
@@ -538,6 +567,7 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
       }
     }
     __syncthreads();
+    CGS_TRACE(j, 9);
     double* t = s_rcol;
     s_rcol = s_rnext;
     s_rnext = t;

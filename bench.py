@@ -53,7 +53,8 @@ L2_FLUSH_BYTES = 256 << 20
 # x 2.07 GHz = 1.259 TFLOP/s (the recipe's nominal 1.25 TFLOP/s FP64).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_1703_10440_gb300/csrc/mgsa_sweep.cu", "paper_1703_10440_gb300/csrc/mgsa_internal.cuh"]
+KERNEL_SOURCES = ["paper_1703_10440_gb300/csrc/mgsa_sweep.cu", "paper_1703_10440_gb300/csrc/mgsa_internal.cuh",
+                  "paper_1703_10440_gb300/csrc/mgsa_device.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 
 

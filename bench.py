@@ -21,7 +21,9 @@ mgsa_qr_batched call per variant, against one mgsa_qr launch per instance.
 
 ``--workload served`` runs the continuous-batching server on a Poisson stream
 of requests (default 2000/s for 30 s; --serve-rate / --serve-seconds change
-it and are reported in the line) and reports p50 / p99 latency and QRs/s.
+it and are reported in the line) and reports p50 / p99 latency and QRs/s;
+--serve-sweep R1,R2,... serves the stream at several rates and reports each
+sampled request's latency over its own solo latency.
 
 ``--impl reference`` times the CPU oracle (plain C, one core) on the same
 workload: each step is one QR, the variants taking turns.
@@ -459,40 +461,69 @@ def run_batch(args, rank, world, local_rank):
 
 def run_served(args, rank, world, local_rank):
     """Served stream: Poisson arrivals (default 2000/s for 30 s), m ~ logU[1e3, 1e6],
-    n ~ U{8..128}, 50/50 Laplacian / banded, 120 GB admission budget."""
+    n ~ U{8..128}, 50/50 Laplacian / banded, 120 GB admission budget.
+
+    With --serve-sweep R1,R2,... the stream is served at each rate in turn and
+    every sampled request's latency is divided by its own solo latency (the
+    same request served alone on an idle GPU); the line reports, per rate,
+    p50 / p99 latency, p99 of that slowdown and QR/s, the largest rate whose
+    p99 slowdown is at most 2, and serving against one solo call at a time."""
     import torch
 
     from paper_1703_10440_gb300 import mgsa
     from paper_1703_10440_gb300.serve import Request, Server, poisson_arrivals
 
     torch.cuda.set_device(local_rank)
-    reqs = poisson_arrivals(args.serve_rate, args.serve_seconds, seed=W.SEED + rank)
     h = mgsa.Handle(local_rank)
     srv = Server(h.h, args.serve_variant, budget_bytes=120e9, small_work=args.serve_small_work, device=local_rank)
-    # warm-up: a few requests alone
-    srv.run([Request(10**7 + k, r.m, r.n, r.kind, 0.0, r.seed) for k, r in enumerate(reqs[:4])], realtime=False)
-    with ClockSampler(local_rank) as clk:
-        stats = srv.run(reqs, realtime=True)
-    # solo latency of a sample: each request served alone on an idle GPU
+    rates = [float(x) for x in args.serve_sweep.split(",")] if args.serve_sweep else [args.serve_rate]
+    streams = {rate: poisson_arrivals(rate, args.serve_seconds, seed=W.SEED + rank) for rate in rates}
+    warm = streams[rates[0]][:4]
+    srv.run([Request(10**7 + k, r.m, r.n, r.kind, 0.0, r.seed) for k, r in enumerate(warm)], realtime=False)
     g = np.random.Generator(np.random.PCG64(7))
-    sample = [reqs[k] for k in sorted(g.choice(len(reqs), size=min(40, len(reqs)), replace=False))]
-    solo = []
-    for r in sample:
-        one = Request(r.rid, r.m, r.n, r.kind, 0.0, r.seed)
-        st = srv.run([one], realtime=False)
-        solo.append(st["p50_ms"])
+    runs = []
+    with ClockSampler(local_rank) as clk:
+        for rate in rates:
+            reqs = streams[rate]
+            stats = srv.run(reqs, realtime=True)
+            lat = dict(srv.last_latency_s)
+            sample = sorted(g.choice(len(reqs), size=min(args.serve_sample, len(reqs)), replace=False).tolist())
+            runs.append((rate, reqs, stats, lat, sample))
+    # solo latency of every sampled request (sizes depend only on the index)
+    by_rid = {}
+    for rate, reqs, _, _, sample in runs:
+        for k in sample:
+            by_rid.setdefault(reqs[k].rid, reqs[k])
+    solo = {}
+    for rid, r in sorted(by_rid.items()):
+        srv.run([Request(r.rid, r.m, r.n, r.kind, 0.0, r.seed)], realtime=False)
+        solo[rid] = srv.last_latency_s[rid]
     h.close()
     if rank != 0:
         return
-    solo_med = float(np.median(solo))
-    line = {"metric": METRIC, "value": stats["qr_per_s"] * world, "unit": UNIT, "n_gpus": world, "steps": 1,
-            "warmup": 1, "ms_per_step": stats["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+    sweep = []
+    for rate, reqs, stats, lat, sample in runs:
+        slow = np.array([lat[reqs[k].rid] / solo[reqs[k].rid] for k in sample])
+        sweep.append({"rate_per_s": rate, "requests": stats["requests"], "ok": stats["ok"],
+                      "qr_per_s": stats["qr_per_s"], "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
+                      "p50_slowdown": float(np.percentile(slow, 50)), "p99_slowdown": float(np.percentile(slow, 99)),
+                      "slowdown_sample": len(sample), "launches": stats["launches"], "small": stats["small"],
+                      "peak_bytes": stats["peak_bytes"]})
+    solo_s = np.array(list(solo.values()))
+    serial_qr_per_s = len(solo_s) / float(solo_s.sum())
+    ok_rates = [x["rate_per_s"] for x in sweep if x["p99_slowdown"] <= 2.0]
+    main = sweep[-1]
+    line = {"metric": METRIC, "value": main["qr_per_s"] * world, "unit": UNIT, "n_gpus": world, "steps": 1,
+            "warmup": 1, "ms_per_step": runs[-1][2]["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "served_poisson_m1e3-1e6_n8-128_laplace/banded", "rate_per_s": args.serve_rate,
-                       "seconds": args.serve_seconds, "requests": stats["requests"], "variant": args.serve_variant,
+            "config": {"workload": "served_poisson_m1e3-1e6_n8-128_laplace/banded", "rate_per_s": main["rate_per_s"],
+                       "seconds": args.serve_seconds, "requests": main["requests"], "variant": args.serve_variant,
                        "budget_gb": 120, "small_work": args.serve_small_work},
-            "served": {**stats, "solo_p50_ms_sample": solo_med, "p99_over_solo": stats["p99_ms"] / solo_med},
-            "gpu_launches": stats["launches"], "clocks": clk.summary()}
+            "served": {"sweep": sweep, "solo_p50_ms": float(np.median(solo_s) * 1e3),
+                       "solo_serial_qr_per_s": serial_qr_per_s,
+                       "served_over_serial": main["qr_per_s"] / serial_qr_per_s,
+                       "max_rate_p99_slowdown_le_2": max(ok_rates) if ok_rates else None},
+            "gpu_launches": int(sum(x["launches"] for x in sweep)), "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -508,6 +539,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="served: arrival window")
     ap.add_argument("--serve-variant", default="hp", choices=["naive", "ha", "hp"])
     ap.add_argument("--serve-small-work", type=float, default=2e7, help="served: m*n^2 up to which the batched kernel runs")
+    ap.add_argument("--serve-sweep", default="", help="served: comma-separated arrival rates run in turn")
+    ap.add_argument("--serve-sample", type=int, default=200, help="served: requests per rate timed alone as well")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

@@ -57,16 +57,19 @@ class Request:
 def poisson_arrivals(rate: float, duration: float, seed: int = 20170330, m_lo: float = 1e3, m_hi: float = 1e6,
                      n_lo: int = 8, n_hi: int = 128) -> list[Request]:
     """Arrivals of a Poisson process of ``rate`` per second over ``duration``
-    seconds; m ~ logU[m_lo, m_hi], n ~ U{n_lo..n_hi}, matrix kind 50/50."""
-    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 50])))
+    seconds; m ~ logU[m_lo, m_hi], n ~ U{n_lo..n_hi}, matrix kind 50/50.  The
+    sizes and the gaps come from separate streams, so request k has the same
+    size at every rate (only its arrival time depends on the rate)."""
+    gaps = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 50])))
+    sizes = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 51])))
     t, out = 0.0, []
     while True:
-        t += g.exponential(1.0 / rate)
+        t += gaps.exponential(1.0 / rate)
         if t >= duration:
             break
-        m = int(round(math.exp(g.uniform(math.log(m_lo), math.log(m_hi)))))
-        n = int(g.integers(n_lo, n_hi + 1))
-        kind = "laplace" if g.random() < 0.5 else "banded"
+        m = int(round(math.exp(sizes.uniform(math.log(m_lo), math.log(m_hi)))))
+        n = int(sizes.integers(n_lo, n_hi + 1))
+        kind = "laplace" if sizes.random() < 0.5 else "banded"
         out.append(Request(len(out), m, n, kind, t, seed))
     return out
 
@@ -213,6 +216,7 @@ class Server:
         lat = np.array([r.t_done - r.arrival for r in requests])
         first = min(r.arrival for r in requests)
         last = max(r.t_done for r in requests)
+        self.last_latency_s = {r.rid: r.t_done - r.arrival for r in requests}
         return {"requests": len(requests), "ok": int(sum(r.info == 0 for r in requests)),
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "mean_ms": float(lat.mean() * 1e3), "qr_per_s": len(requests) / (last - first),

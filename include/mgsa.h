@@ -234,20 +234,31 @@ size_t mgsa_job_workspace_bytes(int64_t m, int n, mgsa_variant v);
  * count < 0 or NULL arrays (count > 0); count == 0 does nothing. */
 mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, int* info_dev, mgsa_stream_t s);
 
-/* Launch parameters of the single-instance kernel (0 restores the default).
- *   MGSA_PARAM_MAX_CTAS          cap on the number of CTAs (default: one per
- *                                SM that fits, i.e. the co-resident maximum)
+/* Launch parameters (0 restores the default).
+ *   MGSA_PARAM_MAX_CTAS          cap on the number of CTAs of a single-instance
+ *                                launch (default: one per SM that fits, i.e.
+ *                                the co-resident maximum)
  *   MGSA_PARAM_CHUNK_ROWS        rows whose pivot vectors are staged in shared
  *                                memory at once (multiple of 32, <= 4096)
  *   MGSA_PARAM_MIN_ROWS_PER_CTA  smallest row slab given to one CTA (default 128,
  *                                or 32 when A averages >= 32 nonzeros per row)
- * Results stay deterministic for a fixed setting; different settings change the
- * reduction tree and therefore the last bits of Q and R.  Returns
- * MGSA_ERR_INVALID for an unknown parameter or an out-of-range value. */
+ *   MGSA_PARAM_BATCH_CTAS        cap on the number of CTAs of mgsa_qr_batched
+ *                                launches (default: one per SM).  With
+ *                                MAX_CTAS on another handle, the two kinds of
+ *                                launch can run side by side on disjoint SMs
+ *                                (their CTA counts summing to at most the SM
+ *                                count), which a server uses to keep small
+ *                                requests from waiting behind large ones.
+ * Results stay deterministic for a fixed setting; different MAX_CTAS,
+ * CHUNK_ROWS or MIN_ROWS_PER_CTA settings change the reduction tree and
+ * therefore the last bits of Q and R (BATCH_CTAS does not: one CTA runs one
+ * instance).  Returns MGSA_ERR_INVALID for an unknown parameter or an
+ * out-of-range value. */
 typedef enum {
   MGSA_PARAM_MAX_CTAS = 0,
   MGSA_PARAM_CHUNK_ROWS = 1,
-  MGSA_PARAM_MIN_ROWS_PER_CTA = 2
+  MGSA_PARAM_MIN_ROWS_PER_CTA = 2,
+  MGSA_PARAM_BATCH_CTAS = 3
 } mgsa_param;
 mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value);
 

@@ -20,7 +20,8 @@ struct mgsa_context {
   int chunk_rows = 0;          // MGSA_PARAM_CHUNK_ROWS (0 = kMaxChunk)
   int64_t min_rows = 0;        // MGSA_PARAM_MIN_ROWS_PER_CTA (0 = kMinRowsPerCta)
   double* batch_scratch = nullptr;  // per-CTA partial sums of the batched kernels
-  int batch_grid = 0;               // CTAs of a batched launch
+  int batch_grid = 0;               // CTAs of a batched launch (co-resident maximum)
+  int64_t batch_ctas = 0;           // MGSA_PARAM_BATCH_CTAS (0 = batch_grid)
   size_t batch_smem = 0;
 };
 
@@ -250,6 +251,7 @@ mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value) {
       h->chunk_rows = (int)value;
       return MGSA_OK;
     case MGSA_PARAM_MIN_ROWS_PER_CTA: h->min_rows = value; return MGSA_OK;
+    case MGSA_PARAM_BATCH_CTAS: h->batch_ctas = value; return MGSA_OK;
     default: return fail(MGSA_ERR_INVALID, "unknown parameter");
   }
 }
@@ -383,7 +385,8 @@ mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, 
   ba.scratch_stride = kBatchStride;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
   cudaError_t e = cudaMemsetAsync(ba.queue, 0, 3 * sizeof(unsigned int), cs);
-  if (e == cudaSuccess) e = mgsa::batch_launch(ba, h->batch_grid, h->batch_smem, cs);
+  const int grid = h->batch_ctas > 0 ? (int)std::min<int64_t>(h->batch_ctas, h->batch_grid) : h->batch_grid;
+  if (e == cudaSuccess) e = mgsa::batch_launch(ba, grid, h->batch_smem, cs);
   if (e != cudaSuccess) return cuda_fail(e);
   return MGSA_OK;
 }

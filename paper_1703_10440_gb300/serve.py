@@ -10,6 +10,13 @@ that asks for many A-orthonormalisations of different sizes.  The server:
   into ONE ``mgsa_qr_batched`` call -- a persistent kernel in which every CTA
   runs one instance, so requests of different sizes run side by side -- and
   gives each large request its own ``mgsa_qr`` launch over the whole GPU;
+* with ``max_large_inflight`` = w > 0, keeps at most w large launches queued
+  on the device and launches the waiting large request with the least work
+  (m * n^2) next, so medium requests overtake queued big ones;
+* with ``small_ctas`` = k > 0, partitions the SMs: large requests run with
+  k fewer CTAs than the GPU has SMs, small ones on a second stream and a
+  second handle whose batched launches use k CTAs, so the two kinds run side
+  by side and small requests do not wait behind large ones;
 * keeps ticking while earlier launches run (continuous batching): requests
   that arrive meanwhile are admitted as memory frees up and launched behind
   the work in flight;
@@ -76,7 +83,8 @@ def poisson_arrivals(rate: float, duration: float, seed: int = 20170330, m_lo: f
 
 class Server:
     def __init__(self, handle: int, variant: str = "hp", budget_bytes: float = 120e9, small_work: float = 2e7,
-                 device: int = 0, max_batch: int = 4096, max_m: int = 1_000_000, max_n: int = 128):
+                 device: int = 0, max_batch: int = 4096, max_m: int = 1_000_000, max_n: int = 128,
+                 small_ctas: int = 0, max_large_inflight: int = 0):
         import torch
 
         self.torch = torch
@@ -89,9 +97,30 @@ class Server:
         self.max_batch = max_batch
         self.stream = torch.cuda.Stream(self.dev)
         self.gen_stream = torch.cuda.Stream(self.dev)
+        self.small_ctas = small_ctas
+        self.max_large_inflight = max_large_inflight
+        self.h_small, self.stream_small, self._own_handle = handle, self.stream, 0
+        if small_ctas > 0:
+            sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
+            if not 0 < small_ctas < sms:
+                raise ValueError("small_ctas must be in (0, number of SMs)")
+            mgsa.mgsa_set_param(handle, mgsa.MGSA_PARAM_MAX_CTAS, sms - small_ctas)
+            self._own_handle = mgsa.mgsa_create(device)
+            mgsa.mgsa_set_param(self._own_handle, mgsa.MGSA_PARAM_BATCH_CTAS, small_ctas)
+            self.h_small = self._own_handle
+            self.stream_small = torch.cuda.Stream(self.dev)
         # Large requests share the handle's workspace: size it once, up front.
         mgsa.mgsa_reserve(handle, max_m, max_n, self.v)
         self.shared_ws = mgsa.mgsa_workspace_bytes(handle, max_m, max_n, self.v)
+
+    def close(self):
+        """Undo the SM partition (the caller's handle gets its default CTA count back)."""
+        if self._own_handle:
+            self.torch.cuda.synchronize(self.dev)
+            mgsa.mgsa_set_param(self.h, mgsa.MGSA_PARAM_MAX_CTAS, 0)
+            mgsa.mgsa_destroy(self._own_handle)
+            self._own_handle = 0
+            self.h_small = self.h
 
     # -- admission ---------------------------------------------------------
     def _bytes(self, r: Request) -> int:
@@ -126,6 +155,8 @@ class Server:
         ready = torch.cuda.Event()
         ready.record(self.gen_stream)
         self.stream.wait_event(ready)
+        if self.stream_small is not self.stream:
+            self.stream_small.wait_event(ready)
         groups = []
         small = [r for r in admitted if r.small]
         large = [r for r in admitted if not r.small]
@@ -138,14 +169,14 @@ class Server:
                            r.Q.data_ptr(), r.Q.stride(0), r.R.data_ptr(), r.n, r.work.data_ptr())
             # pinned + non_blocking: the host loop must not wait behind the work in flight
             jobs_host = torch.from_numpy(jobs.view(np.uint8).copy()).pin_memory()
-            with torch.cuda.stream(self.stream):
+            with torch.cuda.stream(self.stream_small):
                 jobs_dev = jobs_host.to(self.dev, non_blocking=True)
                 info = torch.zeros(len(small), dtype=torch.int32, device=self.dev)
-            st = mgsa.mgsa_qr_batched(self.h, len(small), jobs_dev, info, self.stream)
+            st = mgsa.mgsa_qr_batched(self.h_small, len(small), jobs_dev, info, self.stream_small)
             if st != mgsa.MGSA_OK:
                 raise mgsa.MgsaError(st, mgsa.mgsa_last_error())
             done = torch.cuda.Event(enable_timing=True)
-            done.record(self.stream)
+            done.record(self.stream_small)
             groups.append(("batch", small, done, (jobs_dev, info, jobs_host)))
         for r in large:
             rowptr, col, val = r.A
@@ -167,6 +198,7 @@ class Server:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting: collections.deque = collections.deque()
         inflight: collections.deque = collections.deque()
+        ready_large: list = []  # admitted large requests not yet launched (max_large_inflight > 0)
         used = self.shared_ws
         peak = used
         torch.cuda.synchronize(self.dev)
@@ -175,14 +207,14 @@ class Server:
         ref.synchronize()
         t0 = time.perf_counter()
         ticks = launches = 0
-        while pending or waiting or inflight:
+        while pending or waiting or inflight or ready_large:
             now = time.perf_counter() - t0
             while pending and (not realtime or pending[0].arrival <= now):
                 waiting.append(pending.popleft())
             admitted = []
             while waiting and len(admitted) < self.max_batch:
                 need = self._bytes(waiting[0])
-                if used + need > self.budget and (inflight or admitted):
+                if used + need > self.budget and (inflight or admitted or ready_large):
                     break
                 r = waiting.popleft()
                 self._materialize(r)
@@ -190,14 +222,26 @@ class Server:
                 used += need
                 admitted.append(r)
             peak = max(peak, used)
-            if admitted:
-                for g in self._launch(admitted, ref):
+            launch_now = admitted
+            if self.max_large_inflight > 0:
+                ready_large.extend(r for r in admitted if not r.small)
+                launch_now = [r for r in admitted if r.small]
+                n_large = sum(1 for grp in inflight if grp[0] == "single")
+                while ready_large and n_large < self.max_large_inflight:
+                    nxt = min(ready_large, key=lambda r: (r.m * r.n ** 2, r.arrival))
+                    ready_large.remove(nxt)
+                    launch_now.append(nxt)
+                    n_large += 1
+            if launch_now:
+                for g in self._launch(launch_now, ref):
                     inflight.append(g)
                     launches += 1
                 ticks += 1
-            progressed = bool(admitted)
-            while inflight and inflight[0][2].query():
-                kind, reqs, done, extra = inflight.popleft()
+            progressed = bool(launch_now)
+            finished = [grp for grp in inflight if grp[2].query()]
+            if finished:
+                inflight = collections.deque(grp for grp in inflight if not any(grp is f for f in finished))
+            for kind, reqs, done, extra in finished:
                 t_done = ref.elapsed_time(done) / 1e3
                 if kind == "batch":
                     infos = extra[1].cpu().numpy()

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+import workloads as W
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -72,3 +73,72 @@ def test_admission_under_a_tight_budget(handle):
     assert stats["ok"] == len(reqs)
     biggest = max(srv._bytes(r) for r in reqs)
     assert stats["peak_bytes"] <= 2.5e8 + biggest
+
+
+def test_partitioned_sms(handle):
+    """small_ctas: large requests on the other SMs, small ones on their own
+    stream and handle at the same time.  Each result is the same alone and in
+    the mix (same partition); small requests are bitwise the results of an
+    unpartitioned server (one CTA runs one instance either way), large ones
+    agree with it to rounding; and all match the oracle's invariants."""
+    reqs = make_requests()
+    kw = dict(budget_bytes=8e9, small_work=5e6, max_m=60000, max_n=48)
+    mix = KeepingServer(handle.h, "hp", small_ctas=16, **kw)
+    try:
+        stats = mix.run(fresh(reqs), realtime=True)
+        assert stats["ok"] == len(reqs) and 0 < stats["small"] < len(reqs)
+        alone = KeepingServer(handle.h, "hp", small_ctas=16, **kw)
+        try:
+            for r in fresh(reqs):
+                alone.run([Request(r.rid, r.m, r.n, r.kind, 0.0, r.seed)], realtime=False)
+        finally:
+            alone.close()
+    finally:
+        mix.close()
+    plain = KeepingServer(handle.h, "hp", **kw)
+    plain.run(fresh(reqs), realtime=False)
+    for r in reqs:
+        Q, R, info = mix.results[r.rid]
+        Qa, Ra, _ = alone.results[r.rid]
+        Qp, Rp, _ = plain.results[r.rid]
+        assert info == 0
+        assert np.linalg.norm(R - Ra) / np.linalg.norm(Ra) <= 1e-12
+        assert np.abs(Q - Qa).max() <= 1e-10 * np.abs(Qa).max()
+        if r.m * r.n ** 2 <= 5e6:
+            assert np.array_equal(Q, Qp) and np.array_equal(R, Rp)
+        else:
+            assert np.linalg.norm(R - Rp) / np.linalg.norm(Rp) <= 1e-10
+    # the caller's handle is back to its default CTA count
+    A, Z = W.tridiag(3000, 4)
+    d = torch.device("cuda")
+    Ad = tuple(torch.from_numpy(np.ascontiguousarray(x)).to(d) for x in A)
+    Zd = torch.from_numpy(np.ascontiguousarray(Z.T)).to(d).T
+    Q1, R1 = handle.qr(Ad, Zd, "hp")
+    assert handle.info() == (mgsa.MGSA_OK, 0)
+    h2 = mgsa.Handle(0)
+    Q2, R2 = h2.qr(Ad, Zd, "hp")
+    assert h2.info() == (mgsa.MGSA_OK, 0)
+    h2.close()
+    assert torch.equal(Q1, Q2) and torch.equal(R1, R2)
+
+
+def test_shortest_work_first_window(handle):
+    """max_large_inflight: large requests wait on the host and are launched
+    least work first, at most two at a time; results are unchanged."""
+    reqs = make_requests()
+    kw = dict(budget_bytes=8e9, small_work=5e6, max_m=60000, max_n=48)
+    srv = KeepingServer(handle.h, "hp", small_ctas=16, max_large_inflight=2, **kw)
+    try:
+        stats = srv.run(fresh(reqs), realtime=True)
+    finally:
+        srv.close()
+    assert stats["ok"] == len(reqs)
+    plain = KeepingServer(handle.h, "hp", small_ctas=16, **kw)
+    try:
+        plain.run(fresh(reqs), realtime=False)
+    finally:
+        plain.close()
+    for r in reqs:
+        Q, R, _ = srv.results[r.rid]
+        Qp, Rp, _ = plain.results[r.rid]
+        assert np.array_equal(Q, Qp) and np.array_equal(R, Rp)

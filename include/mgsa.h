@@ -249,16 +249,27 @@ mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, 
  *                                (their CTA counts summing to at most the SM
  *                                count), which a server uses to keep small
  *                                requests from waiting behind large ones.
+ *   MGSA_PARAM_ROW_MODE          rows per warp of the MVs and of the block
+ *                                product: 0 = one warp per row when A averages
+ *                                >= 32 nonzeros per row, else one thread per
+ *                                row (default); 1 = one thread per row (32 rows
+ *                                per warp); 2 = one warp per row
+ *   MGSA_PARAM_SPMM_PANEL        columns of Z per pass over A in the block
+ *                                product X = A Z (HP): 4 or 8 (0 = 8); every
+ *                                column's sums are the same for either width
  * Results stay deterministic for a fixed setting; different MAX_CTAS,
- * CHUNK_ROWS or MIN_ROWS_PER_CTA settings change the reduction tree and
- * therefore the last bits of Q and R (BATCH_CTAS does not: one CTA runs one
- * instance).  Returns MGSA_ERR_INVALID for an unknown parameter or an
+ * CHUNK_ROWS, MIN_ROWS_PER_CTA or ROW_MODE settings change the reduction
+ * tree and therefore the last bits of Q and R (BATCH_CTAS and SPMM_PANEL do
+ * not).  The settings of a handle apply to its mgsa_qr, mgsa_qr_append and
+ * (ROW_MODE, SPMM_PANEL, BATCH_CTAS) mgsa_qr_batched calls.  Returns MGSA_ERR_INVALID for an unknown parameter or an
  * out-of-range value. */
 typedef enum {
   MGSA_PARAM_MAX_CTAS = 0,
   MGSA_PARAM_CHUNK_ROWS = 1,
   MGSA_PARAM_MIN_ROWS_PER_CTA = 2,
-  MGSA_PARAM_BATCH_CTAS = 3
+  MGSA_PARAM_BATCH_CTAS = 3,
+  MGSA_PARAM_ROW_MODE = 4,
+  MGSA_PARAM_SPMM_PANEL = 5
 } mgsa_param;
 mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value);
 

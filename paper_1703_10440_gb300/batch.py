@@ -46,6 +46,9 @@ class Batch:
             variants = [variants] * count
         self.count = count
         self.shapes = []
+        self.nnz = [len(A[1]) for A, _ in instances]
+        self.variants = [v if isinstance(v, str) else {i: k for k, i in mgsa.VARIANTS.items()}.get(int(v), str(v))
+                         for v in variants]
         off_rp = off_col = off_val = off_z = off_r = off_w = 0
         layout = []
         for (A, Z), v in zip(instances, variants):

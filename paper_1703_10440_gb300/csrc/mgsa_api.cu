@@ -22,6 +22,8 @@ struct mgsa_context {
   double* batch_scratch = nullptr;  // per-CTA partial sums of the batched kernels
   int batch_grid = 0;               // CTAs of a batched launch (co-resident maximum)
   int64_t batch_ctas = 0;           // MGSA_PARAM_BATCH_CTAS (0 = batch_grid)
+  int row_mode = 0;                 // MGSA_PARAM_ROW_MODE
+  int spmm_panel = 8;               // MGSA_PARAM_SPMM_PANEL
   size_t batch_smem = 0;
 };
 
@@ -103,7 +105,7 @@ mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, P
                       int kg = 0) {
   const int nt = kg + n;
   const int chunk_cap = h->chunk_rows > 0 ? h->chunk_rows : mgsa::kMaxChunk;
-  const bool long_rows = nnz >= (int64_t)mgsa::kWarpRowNnz * m;
+  const bool long_rows = h->row_mode == 0 ? nnz >= (int64_t)mgsa::kWarpRowNnz * m : h->row_mode == 2;
   const int64_t min_rows = h->min_rows > 0 ? h->min_rows : (long_rows ? mgsa::kMinRowsLongRows : mgsa::kMinRowsPerCta);
   int max_ctas = 0;
   const int kv = kernel_variant(v);
@@ -252,6 +254,14 @@ mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value) {
       return MGSA_OK;
     case MGSA_PARAM_MIN_ROWS_PER_CTA: h->min_rows = value; return MGSA_OK;
     case MGSA_PARAM_BATCH_CTAS: h->batch_ctas = value; return MGSA_OK;
+    case MGSA_PARAM_ROW_MODE:
+      if (value > 2) return fail(MGSA_ERR_INVALID, "row mode: 0 (auto), 1 (thread per row) or 2 (warp per row)");
+      h->row_mode = (int)value;
+      return MGSA_OK;
+    case MGSA_PARAM_SPMM_PANEL:
+      if (value != 0 && value != 4 && value != 8) return fail(MGSA_ERR_INVALID, "SpMM panel: 0 (default 8), 4 or 8");
+      h->spmm_panel = value == 0 ? 8 : (int)value;
+      return MGSA_OK;
     default: return fail(MGSA_ERR_INVALID, "unknown parameter");
   }
 }
@@ -323,7 +333,8 @@ static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, 
   a.ctl = h->ctl;
   a.rpc = p.rpc;
   a.chunk = p.chunk;
-  a.mv_warp = A->nnz >= (int64_t)mgsa::kWarpRowNnz * m;
+  a.mv_warp = h->row_mode == 0 ? A->nnz >= (int64_t)mgsa::kWarpRowNnz * m : h->row_mode == 2;
+  a.spmm_panel = h->spmm_panel;
   if (is_cgs(v)) {
     a.qp = a.X + p.ldx * p.xcols;
     a.stages = p.stages;
@@ -383,6 +394,8 @@ mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, 
   ba.queue = reinterpret_cast<unsigned int*>(h->ctl + kBatchQueueWord);
   ba.scratch = h->batch_scratch;
   ba.scratch_stride = kBatchStride;
+  ba.row_mode = h->row_mode;
+  ba.spmm_panel = h->spmm_panel;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
   cudaError_t e = cudaMemsetAsync(ba.queue, 0, 3 * sizeof(unsigned int), cs);
   const int grid = h->batch_ctas > 0 ? (int)std::min<int64_t>(h->batch_ctas, h->batch_grid) : h->batch_grid;

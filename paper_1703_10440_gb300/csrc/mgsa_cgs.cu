@@ -423,7 +423,7 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
   if (b == 0) {
     for (int64_t t = tid; t < (int64_t)n * n; t += kThreads) R[(t % n) + (t / n) * ldr] = 0.0;
   }
-  if (V == kHP) (void)spmm_slab(rowptr, colidx, val, Z, ldz, X, ldx, nullptr, 0, k0, k1, n, warp_rows);
+  if (V == kHP) (void)spmm_slab(rowptr, colidx, val, Z, ldz, X, ldx, nullptr, 0, k0, k1, n, warp_rows, a.spmm_panel);
   __syncthreads();
 
   // Resident slots: z_j, x_j of the current column and z_{j+1}^{(0)}.

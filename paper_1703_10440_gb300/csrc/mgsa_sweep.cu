@@ -200,7 +200,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     for (int64_t t = tid; t < (int64_t)nt * n; t += kThreads) R[(t % nt) + (t / nt) * ldr] = 0.0;
   }
   if (V == kHP) {
-    const double s0 = spmm_slab(rowptr, colidx, val, Z, ldz, X, ldx, Q, ldq, k0, k1, n, a.mv_warp != 0);
+    const double s0 = spmm_slab(rowptr, colidx, val, Z, ldz, X, ldx, Q, ldq, k0, k1, n, a.mv_warp != 0, a.spmm_panel);
     if (!resident) {
       const double t = block_sum(s0, s_buf);
       if (tid == 0) part_norm[b] = t;
@@ -624,7 +624,8 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_batch_kernel(const BatchArgs 
       a.ctl = nullptr;
       a.rpc = (m + 31) / 32 * 32;
       a.chunk = (int)(a.rpc < kMaxChunk ? a.rpc : kMaxChunk);
-      a.mv_warp = (int64_t)__ldg(J.rowptr + m) >= (int64_t)kWarpRowNnz * m;
+      a.mv_warp = ba.row_mode == 0 ? (int64_t)__ldg(J.rowptr + m) >= (int64_t)kWarpRowNnz * m : ba.row_mode == 2;
+      a.spmm_panel = ba.spmm_panel;
       result = sweep_body<V, true>(a, 1, 0, smem, s_wfirst, s_wlast, s_flags);
     }
     if (threadIdx.x == 0) {

@@ -79,7 +79,8 @@ SIGNATURES = {
                               _VP, _I64, _VP, _I64, _VP, _INT, _VP]),
     "mgsa_last_error": (ctypes.c_char_p, []),
 }
-MGSA_PARAM_MAX_CTAS, MGSA_PARAM_CHUNK_ROWS, MGSA_PARAM_MIN_ROWS_PER_CTA, MGSA_PARAM_BATCH_CTAS = 0, 1, 2, 3
+(MGSA_PARAM_MAX_CTAS, MGSA_PARAM_CHUNK_ROWS, MGSA_PARAM_MIN_ROWS_PER_CTA, MGSA_PARAM_BATCH_CTAS, MGSA_PARAM_ROW_MODE,
+ MGSA_PARAM_SPMM_PANEL) = 0, 1, 2, 3, 4, 5
 
 
 def library_path() -> str:

@@ -114,7 +114,9 @@ size_t mgsa_workspace_bytes(mgsa_handle h, int64_t m, int n, mgsa_variant v);
  *
  *   A      CSR matrix with A->m == m (device arrays, read only).
  *   Z      m x n input, column-major, leading dimension ldz >= m (read only).
- *   Q      m x n output, leading dimension ldq >= m.  Must not overlap Z.
+ *   Q      m x n output, leading dimension ldq >= m.  Either Z itself (Q == Z
+ *          and ldq == ldz: the factorisation runs in place) or not
+ *          overlapping Z at all.
  *          Q is also the working storage of the z_j^{(i)} columns.
  *   R      n x n output, leading dimension ldr >= n; written in full, zeros
  *          below the diagonal.

@@ -292,7 +292,11 @@ static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, 
   if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return fail(MGSA_ERR_INVALID, "NULL CSR array");
   const size_t zspan = sizeof(double) * (size_t)((n - 1) * ldz + m);
   const size_t qspan = sizeof(double) * (size_t)((n - 1) * ldq + m);
-  if (ranges_overlap(Z, zspan, Q, qspan)) return fail(MGSA_ERR_INVALID, "Q overlaps Z");
+  // Q may be Z itself (same pointer and leading dimension): the kernels read
+  // Z only before their first device-wide wait, or only columns they have not
+  // yet written.  Any other overlap is refused.
+  const bool in_place = static_cast<const void*>(Q) == static_cast<const void*>(Z) && ldq == ldz;
+  if (!in_place && ranges_overlap(Z, zspan, Q, qspan)) return fail(MGSA_ERR_INVALID, "Q overlaps Z");
   const size_t rspan = sizeof(double) * (size_t)((int64_t)(n - 1) * ldr + nt);
   if (ranges_overlap(R, rspan, Q, qspan) || ranges_overlap(R, rspan, Z, zspan))
     return fail(MGSA_ERR_INVALID, "R overlaps Q or Z");

@@ -80,8 +80,9 @@ extern "C" mgsa_status mgsa_qr_noalloc(const mgsa_csr* A, const double* Z, int64
   const size_t zspan = sizeof(double) * (size_t)((n - 1) * ldz + m);
   const size_t qspan = sizeof(double) * (size_t)((n - 1) * ldq + m);
   const size_t rspan = sizeof(double) * (size_t)((int64_t)(n - 1) * ldr + n);
-  if (overlap(Z, zspan, Q, qspan) || overlap(R, rspan, Q, qspan) || overlap(R, rspan, Z, zspan))
-    return fail(MGSA_ERR_INVALID, "Q, R and Z must not overlap");
+  const bool in_place = static_cast<const void*>(Q) == static_cast<const void*>(Z) && ldq == ldz;  // Q = Z allowed
+  if ((!in_place && overlap(Z, zspan, Q, qspan)) || overlap(R, rspan, Q, qspan) || overlap(R, rspan, Z, zspan))
+    return fail(MGSA_ERR_INVALID, "Q, R and Z must not overlap (Q may be Z itself)");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

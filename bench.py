@@ -333,7 +333,8 @@ def run_gpu(args, desc, A, Z, rank, world, local_rank):
         ms = per_variant_ms[vi]
         gbs = b / ms / 1e6
         tfl = fl / ms / 1e9
-        per_variant[v] = {"ms": round(ms, 4), "qr_per_s": round(1e3 / ms, 2), "model_bytes": b, "model_flops": fl,
+        per_variant[v] = {"ms": round(ms, 4), "qr_per_s": round(1e3 / ms, 2), "cols_per_s": round(n * 1e3 / ms, 1),
+                          "model_bytes": b, "model_flops": fl,
                           "model_GBs": round(gbs, 1), "hbm_frac": round(gbs / peak_hbm, 4),
                           "fp64_tflops": round(tfl, 4), "fp64_frac": round(tfl / FP64_PEAK_TFLOPS, 4)}
     # Dominant kernel: the longest of the three launches of a step.
@@ -438,6 +439,7 @@ def run_batch(args, rank, world, local_rank):
         fl = sum(model(v, m, n, z)[1] for (m, n), z in zip(ms_sizes, nnz))
         tfl = fl / per_ms[vi] / 1e9
         per_variant[v] = {"ms": round(per_ms[vi], 3), "qr_per_s": round(len(inst) * 1e3 / per_ms[vi], 1),
+                          "cols_per_s": round(sum(n for _, n in ms_sizes) * 1e3 / per_ms[vi], 1),
                           "model_flops": fl, "fp64_tflops": round(tfl, 4),
                           "fp64_frac": round(tfl / FP64_PEAK_TFLOPS, 4)}
     step_ms = sum(per_ms)

@@ -176,8 +176,12 @@ def test_invalid_arguments_rejected_before_launch(handle):
     for b in bad:
         st = mgsa.mgsa_qr(handle.h, csr, Zd, b["m"], b["n"], b["ldz"], mgsa.MGSA_HP, Q, b["ldq"], R, b["ldr"])
         assert st == mgsa.MGSA_ERR_INVALID, b
-    # Q overlapping Z
-    st = mgsa.mgsa_qr(handle.h, csr, Zd, 64, 8, 64, mgsa.MGSA_HP, Zd, 64, R, 8)
+    # Q overlapping Z without being Z itself (Q == Z runs in place, tests/test_gpu_inplace.py)
+    buf = torch.zeros(9 * 64, dtype=torch.float64, device="cuda")
+    Zb = buf[: 8 * 64].view(8, 64).T
+    Zb.copy_(Zd)
+    Qs = buf[32: 32 + 8 * 64].view(8, 64).T
+    st = mgsa.mgsa_qr(handle.h, csr, Zb, 64, 8, 64, mgsa.MGSA_HP, Qs, 64, R, 8)
     assert st == mgsa.MGSA_ERR_INVALID
     # A->m mismatch
     csr_bad = mgsa.make_csr(65, len(A[1]), *Ad)

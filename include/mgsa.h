@@ -257,8 +257,9 @@ mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, 
  *                                row (default); 1 = one thread per row (32 rows
  *                                per warp); 2 = one warp per row
  *   MGSA_PARAM_SPMM_PANEL        columns of Z per pass over A in the block
- *                                product X = A Z (HP): 4 or 8 (0 = 8); every
- *                                column's sums are the same for either width
+ *                                product X = A Z (HP): 4 or 8 (0 = 8), each
+ *                                width a kernel of its own; every column's
+ *                                sums are the same for either width
  * Results stay deterministic for a fixed setting; different MAX_CTAS,
  * CHUNK_ROWS, MIN_ROWS_PER_CTA or ROW_MODE settings change the reduction
  * tree and therefore the last bits of Q and R (BATCH_CTAS and SPMM_PANEL do

@@ -360,7 +360,7 @@ __device__ double mv_rows(const int32_t* __restrict__ rowptr, const int32_t* __r
   return sl;
 }
 
-template <int V>
+template <int V, int kPanel>
 __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* smem, uint64_t* s_full,
                         uint64_t* s_empty, int* s_flags) {
   const int n = a.n;
@@ -423,7 +423,7 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
   if (b == 0) {
     for (int64_t t = tid; t < (int64_t)n * n; t += kThreads) R[(t % n) + (t / n) * ldr] = 0.0;
   }
-  if (V == kHP) (void)spmm_slab(rowptr, colidx, val, Z, ldz, X, ldx, nullptr, 0, k0, k1, n, warp_rows, a.spmm_panel);
+  if (V == kHP) (void)spmm_slab_panel<kPanel>(rowptr, colidx, val, Z, ldz, X, ldx, nullptr, 0, k0, k1, n, warp_rows);
   __syncthreads();
 
   // Resident slots: z_j, x_j of the current column and z_{j+1}^{(0)}.
@@ -579,23 +579,26 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
   return 0;
 }
 
-template <int V>
+template <int V, int kPanel>
 __global__ void __launch_bounds__(kThreads, 1) cgs_sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(16) double smem[];
   __shared__ __align__(8) uint64_t s_full[kCgsMaxStages];
   __shared__ __align__(8) uint64_t s_empty[kCgsMaxStages];
   __shared__ int s_flags[3];  // barrier scratch (2), ring abort flag
-  const int r = cgs_body<V>(a, gridDim.x, blockIdx.x, smem, s_full, s_empty, s_flags);
+  const int r = cgs_body<V, kPanel>(a, gridDim.x, blockIdx.x, smem, s_full, s_empty, s_flags);
   if (r != 0 && (r >> 24) != kDevTimeout && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.ctl, r >> 24, r & 0xFFFFFF);
 }
 
 }  // namespace
 
-static const void* cgs_fn(int variant) {
+// naive and HA have no block product; HP has one kernel per panel width.
+static const void* cgs_fn(int variant, int panel = 8) {
   switch (variant) {
-    case kNaive: return reinterpret_cast<const void*>(cgs_sweep_kernel<kNaive>);
-    case kHA: return reinterpret_cast<const void*>(cgs_sweep_kernel<kHA>);
-    default: return reinterpret_cast<const void*>(cgs_sweep_kernel<kHP>);
+    case kNaive: return reinterpret_cast<const void*>(cgs_sweep_kernel<kNaive, 8>);
+    case kHA: return reinterpret_cast<const void*>(cgs_sweep_kernel<kHA, 8>);
+    default:
+      return panel == 4 ? reinterpret_cast<const void*>(cgs_sweep_kernel<kHP, 4>)
+                        : reinterpret_cast<const void*>(cgs_sweep_kernel<kHP, 8>);
   }
 }
 
@@ -628,11 +631,13 @@ cudaError_t cgs_prepare(int device) {
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e != cudaSuccess) return e;
-  for (int v = kNaive; v <= kHP; ++v) {
+  const int instances[4][2] = {{kNaive, 8}, {kHA, 8}, {kHP, 8}, {kHP, 4}};
+  for (const auto& k : instances) {
+    const void* fn = cgs_fn(k[0], k[1]);
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, cgs_fn(v))) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
     const int dyn = optin - (int)fa.sharedSizeBytes;
-    if ((e = cudaFuncSetAttribute(cgs_fn(v), cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -651,7 +656,7 @@ cudaError_t cgs_max_ctas(int variant, size_t smem, int* max_ctas) {
 cudaError_t cgs_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s) {
   SweepArgs copy = a;
   void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel(cgs_fn(variant), dim3(grid), dim3(kThreads), args, smem, s);
+  return cudaLaunchCooperativeKernel(cgs_fn(variant, a.spmm_panel), dim3(grid), dim3(kThreads), args, smem, s);
 }
 
 }  // namespace mgsa

@@ -361,15 +361,6 @@ __device__ double spmm_slab_panel(const int32_t* __restrict__ rowptr, const int3
   return s0;
 }
 
-// The block product with a panel width of 4 or 8 columns (a launch parameter).
-__device__ __forceinline__ double spmm_slab(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                            const double* __restrict__ val, const double* __restrict__ Z, int64_t ldz,
-                                            double* __restrict__ X, int64_t ldx, double* __restrict__ Q, int64_t ldq,
-                                            int64_t k0, int64_t k1, int n, bool warp_rows, int panel) {
-  if (panel == 4) return spmm_slab_panel<4>(rowptr, colidx, val, Z, ldz, X, ldx, Q, ldq, k0, k1, n, warp_rows);
-  return spmm_slab_panel<8>(rowptr, colidx, val, Z, ldz, X, ldx, Q, ldq, k0, k1, n, warp_rows);
-}
-
 }  // namespace
 
 }  // namespace mgsa

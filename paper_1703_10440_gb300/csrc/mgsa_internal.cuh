@@ -41,7 +41,7 @@ struct SweepArgs {
   int64_t rpc;     // rows per CTA, multiple of 32
   int chunk;       // rows per staged chunk, multiple of 32
   int mv_warp;     // 1: one warp per CSR row in the MVs / block product (long rows)
-  int spmm_panel = 8;  // columns per pass of the block product X = A Z (4 or 8)
+  int spmm_panel = 8;  // columns per pass of the block product X = A Z (4 or 8): selects the HP kernel
   // Successive orthogonalisation: kg given A-orthonormal columns Qg (with Pg =
   // their p_i) come first; the n columns of Z are columns kg .. kg+n-1 of the
   // virtual matrix and R is (kg+n) x n.  kg = 0 for a plain QR.
@@ -97,7 +97,7 @@ struct BatchArgs {
   double* scratch;         // per-CTA partial sums
   int64_t scratch_stride;  // doubles per CTA, >= 2 * max_n + 1
   int row_mode = 0;        // 0: warp per row when nnz >= 32 m, 1: thread per row, 2: warp per row
-  int spmm_panel = 8;      // as SweepArgs::spmm_panel, for every job
+  int spmm_panel = 8;      // as SweepArgs::spmm_panel, for every HP job
 };
 
 // Records the message mgsa_last_error returns on this thread (mgsa_api.cu).

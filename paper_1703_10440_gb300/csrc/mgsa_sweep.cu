@@ -150,7 +150,7 @@ __device__ __forceinline__ void fused_pass(int i, int jbeg, int ncols, int kg, i
 
 // The whole right-looking loop for one instance, run by G CTAs (CTA b owns
 // rows [b*rpc, (b+1)*rpc)).  Returns 0 or body_result(status, column).
-template <int V, bool kBatch>
+template <int V, bool kBatch, int kPanel>
 __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* smem, int* s_wfirst, int* s_wlast,
                           int* s_flags) {
   const int n = a.n;    // columns of Z
@@ -200,7 +200,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     for (int64_t t = tid; t < (int64_t)nt * n; t += kThreads) R[(t % nt) + (t / nt) * ldr] = 0.0;
   }
   if (V == kHP) {
-    const double s0 = spmm_slab(rowptr, colidx, val, Z, ldz, X, ldx, Q, ldq, k0, k1, n, a.mv_warp != 0, a.spmm_panel);
+    const double s0 = spmm_slab_panel<kPanel>(rowptr, colidx, val, Z, ldz, X, ldx, Q, ldq, k0, k1, n, a.mv_warp != 0);
     if (!resident) {
       const double t = block_sum(s0, s_buf);
       if (tid == 0) part_norm[b] = t;
@@ -568,12 +568,13 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
 }
 
 // Single instance over the whole grid (cooperative launch).
-template <int V>
+// kPanel: columns per pass of the block product (HP; one instantiation per width).
+template <int V, int kPanel>
 __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(16) double smem[];
   __shared__ int s_wfirst[kWarps], s_wlast[kWarps];
   __shared__ int s_flags[2];
-  const int r = sweep_body<V, false>(a, gridDim.x, blockIdx.x, smem, s_wfirst, s_wlast, s_flags);
+  const int r = sweep_body<V, false, kPanel>(a, gridDim.x, blockIdx.x, smem, s_wfirst, s_wlast, s_flags);
   // Breakdown verdicts are identical in every CTA; CTA 0 records them.  A
   // timeout was recorded by the CTA that saw it.
   if (r != 0 && (r >> 24) != kDevTimeout && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.ctl, r >> 24, r & 0xFFFFFF);
@@ -583,7 +584,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
 // runs the whole loop of that instance by itself (CTA-wide barriers only).
 // One launch per variant: the launch for V takes the jobs of variant V (the
 // HP launch also answers jobs whose variant is unknown).
-template <int V>
+template <int V, int kPanel>
 __global__ void __launch_bounds__(kThreads, 1) mgs_batch_kernel(const BatchArgs ba) {
   extern __shared__ __align__(16) double smem[];
   __shared__ int s_wfirst[kWarps], s_wlast[kWarps];
@@ -625,8 +626,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_batch_kernel(const BatchArgs 
       a.rpc = (m + 31) / 32 * 32;
       a.chunk = (int)(a.rpc < kMaxChunk ? a.rpc : kMaxChunk);
       a.mv_warp = ba.row_mode == 0 ? (int64_t)__ldg(J.rowptr + m) >= (int64_t)kWarpRowNnz * m : ba.row_mode == 2;
-      a.spmm_panel = ba.spmm_panel;
-      result = sweep_body<V, true>(a, 1, 0, smem, s_wfirst, s_wlast, s_flags);
+      result = sweep_body<V, true, kPanel>(a, 1, 0, smem, s_wfirst, s_wlast, s_flags);
     }
     if (threadIdx.x == 0) {
       int info = 0;
@@ -641,23 +641,40 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_batch_kernel(const BatchArgs 
 
 }  // namespace
 
-static const void* sweep_fn(int variant) {
+// The kernels: naive and HA have no block product; HP has one per panel width.
+static const void* sweep_fn(int variant, int panel = 8) {
   switch (variant) {
-    case kNaive: return reinterpret_cast<const void*>(mgs_sweep_kernel<kNaive>);
-    case kHA: return reinterpret_cast<const void*>(mgs_sweep_kernel<kHA>);
-    default: return reinterpret_cast<const void*>(mgs_sweep_kernel<kHP>);
+    case kNaive: return reinterpret_cast<const void*>(mgs_sweep_kernel<kNaive, 8>);
+    case kHA: return reinterpret_cast<const void*>(mgs_sweep_kernel<kHA, 8>);
+    default:
+      return panel == 4 ? reinterpret_cast<const void*>(mgs_sweep_kernel<kHP, 4>)
+                        : reinterpret_cast<const void*>(mgs_sweep_kernel<kHP, 8>);
   }
 }
+
+static const void* batch_fn(int variant, int panel = 8) {
+  switch (variant) {
+    case kNaive: return reinterpret_cast<const void*>(mgs_batch_kernel<kNaive, 8>);
+    case kHA: return reinterpret_cast<const void*>(mgs_batch_kernel<kHA, 8>);
+    default:
+      return panel == 4 ? reinterpret_cast<const void*>(mgs_batch_kernel<kHP, 4>)
+                        : reinterpret_cast<const void*>(mgs_batch_kernel<kHP, 8>);
+  }
+}
+
+// Every kernel instance: (variant, panel width).
+static const int kKernelInstances[4][2] = {{kNaive, 8}, {kHA, 8}, {kHP, 8}, {kHP, 4}};
 
 cudaError_t sweep_prepare(int device) {
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e != cudaSuccess) return e;
-  for (int v = kNaive; v <= kHP; ++v) {
+  for (const auto& k : kKernelInstances) {
+    const void* fn = sweep_fn(k[0], k[1]);
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, sweep_fn(v))) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
     const int dyn = optin - (int)fa.sharedSizeBytes;  // static shared memory counts against the opt-in limit
-    if ((e = cudaFuncSetAttribute(sweep_fn(v), cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -672,24 +689,16 @@ cudaError_t sweep_max_ctas(int variant, size_t smem, int* max_ctas) {
   return cudaSuccess;
 }
 
-static const void* batch_fn(int variant) {
-  switch (variant) {
-    case kNaive: return reinterpret_cast<const void*>(mgs_batch_kernel<kNaive>);
-    case kHA: return reinterpret_cast<const void*>(mgs_batch_kernel<kHA>);
-    default: return reinterpret_cast<const void*>(mgs_batch_kernel<kHP>);
-  }
-}
-
 cudaError_t batch_prepare(int device, size_t smem) {
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e != cudaSuccess) return e;
-  for (int v = kNaive; v <= kHP; ++v) {
+  for (const auto& k : kKernelInstances) {
+    const void* fn = batch_fn(k[0], k[1]);
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, batch_fn(v))) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
     if (smem + fa.sharedSizeBytes > (size_t)optin) return cudaErrorInvalidValue;
-    if ((e = cudaFuncSetAttribute(batch_fn(v), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-      return e;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -706,16 +715,17 @@ cudaError_t batch_max_ctas(size_t smem, int* max_ctas) {
 }
 
 cudaError_t batch_launch(const BatchArgs& ba, int grid, size_t smem, cudaStream_t s) {
-  mgs_batch_kernel<kNaive><<<grid, kThreads, smem, s>>>(ba);
-  mgs_batch_kernel<kHA><<<grid, kThreads, smem, s>>>(ba);
-  mgs_batch_kernel<kHP><<<grid, kThreads, smem, s>>>(ba);
+  mgs_batch_kernel<kNaive, 8><<<grid, kThreads, smem, s>>>(ba);
+  mgs_batch_kernel<kHA, 8><<<grid, kThreads, smem, s>>>(ba);
+  if (ba.spmm_panel == 4) mgs_batch_kernel<kHP, 4><<<grid, kThreads, smem, s>>>(ba);
+  else mgs_batch_kernel<kHP, 8><<<grid, kThreads, smem, s>>>(ba);
   return cudaGetLastError();
 }
 
 cudaError_t sweep_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s) {
   SweepArgs copy = a;
   void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel(sweep_fn(variant), dim3(grid), dim3(kThreads), args, smem, s);
+  return cudaLaunchCooperativeKernel(sweep_fn(variant, a.spmm_panel), dim3(grid), dim3(kThreads), args, smem, s);
 }
 
 }  // namespace mgsa

@@ -232,6 +232,21 @@ def run_reference(args, desc, A, Z, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def rank_reduce(x: float, op: str, world: int, device) -> float:
+    """x combined over the ranks of the process group: "max" for times (the
+    slowest rank sets the step), "sum" for throughputs.  Identity for one
+    process.  ``device``: where the collective's tensor lives (CUDA for NCCL,
+    CPU for gloo)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def run_gpu(args, desc, A, Z, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -285,10 +300,7 @@ def run_gpu(args, desc, A, Z, rank, world, local_rank):
     per_variant_ms = [sum(ev[k][vi][0].elapsed_time(ev[k][vi][1]) for k in range(args.steps)) / args.steps
                       for vi in range(len(VARIANTS))]
     step_ms = sum(per_variant_ms)
-    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms_max = float(t.item())
+    step_ms_max = rank_reduce(step_ms, "max", world, dev)
 
     # End to end through the host-buffer entry point: copies in, QR, copies out.
     e2e = None
@@ -313,11 +325,7 @@ def run_gpu(args, desc, A, Z, rank, world, local_rank):
         for _ in range(ksteps):
             e2e_step()
         torch.cuda.synchronize(dev)
-        e2e_ms = 1e3 * (time.perf_counter() - t0) / ksteps
-        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_ms = float(te.item())
+        e2e_ms = rank_reduce(1e3 * (time.perf_counter() - t0) / ksteps, "max", world, dev)
         h2d = 3 * (rowptr.nbytes + col.nbytes + val.nbytes + Z.nbytes)
         d2h = 3 * (8 * m * n + 8 * n * n)
         e2e = {"value": world * 3 * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -371,6 +379,7 @@ def run_gpu(args, desc, A, Z, rank, world, local_rank):
 def run_batch(args, rank, world, local_rank):
     """Batched path: one mgsa_qr_batched call per variant over 4096 instances."""
     import torch
+    import torch.distributed as dist
 
     from paper_1703_10440_gb300 import mgsa
     from paper_1703_10440_gb300.batch import Batch
@@ -395,6 +404,9 @@ def run_batch(args, rank, world, local_rank):
             raise RuntimeError(f"{bad} batched {v} jobs failed")
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in VARIANTS]
           for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
     with ClockSampler(local_rank) as clk:
         for k in range(args.steps):
             for vi, v in enumerate(VARIANTS):
@@ -403,8 +415,11 @@ def run_batch(args, rank, world, local_rank):
                 batches[v].run(h.h, stream)
                 ev[k][vi][1].record(stream)
         torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
     per_ms = [sum(ev[k][vi][0].elapsed_time(ev[k][vi][1]) for k in range(args.steps)) / args.steps
               for vi in range(len(VARIANTS))]
+    step_ms_max = rank_reduce(sum(per_ms), "max", world, dev)
     # One launch per instance (the single-instance entry point), same inputs.
     single_ms = {}
     for v in ("hp",):
@@ -442,10 +457,9 @@ def run_batch(args, rank, world, local_rank):
                           "cols_per_s": round(sum(n for _, n in ms_sizes) * 1e3 / per_ms[vi], 1),
                           "model_flops": fl, "fp64_tflops": round(tfl, 4),
                           "fp64_frac": round(tfl / FP64_PEAK_TFLOPS, 4)}
-    step_ms = sum(per_ms)
     dom = max(VARIANTS, key=lambda v: per_variant[v]["ms"])
-    line = {"metric": METRIC, "value": 3 * len(inst) * 1e3 / step_ms, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+    line = {"metric": METRIC, "value": world * 3 * len(inst) * 1e3 / step_ms_max, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batch4096_banded_hb8_m256-8192_n4-64", "instances": len(inst),
                        "step": "one mgsa_qr_batched call per variant (naive, ha, hp)",
@@ -503,6 +517,7 @@ def run_served(args, rank, world, local_rank):
         solo[rid] = srv.last_latency_s[rid]
     srv.close()
     h.close()
+    total_qr_per_s = rank_reduce(runs[-1][2]["qr_per_s"], "sum", world, torch.device("cuda", local_rank))
     if rank != 0:
         return
     sweep = []
@@ -521,7 +536,7 @@ def run_served(args, rank, world, local_rank):
     ok_rates = [x["rate_per_s"] for x in sweep if x["p99_slowdown"] <= 2.0]
     ok_rates_dist = [x["rate_per_s"] for x in sweep if x["p99_over_solo_p99"] <= 2.0]
     main = sweep[-1]
-    line = {"metric": METRIC, "value": main["qr_per_s"] * world, "unit": UNIT, "n_gpus": world, "steps": 1,
+    line = {"metric": METRIC, "value": total_qr_per_s, "unit": UNIT, "n_gpus": world, "steps": 1,
             "warmup": 1, "ms_per_step": runs[-1][2]["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "served_poisson_m1e3-1e6_n8-128_laplace/banded", "rate_per_s": main["rate_per_s"],

@@ -37,7 +37,7 @@
 // the traced build exports through mgsa_trace_fetch.  The product build
 // contains neither.
 #ifdef MGSA_PHASE_TRACE
-__device__ unsigned long long g_mgsa_trace[4200][12];
+__device__ unsigned long long g_mgsa_trace[4200][16];
 extern "C" int mgsa_trace_fetch(unsigned long long* host) {
   return (int)cudaMemcpyFromSymbol(host, g_mgsa_trace, sizeof(g_mgsa_trace));
 }
@@ -327,10 +327,13 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
             }
           }
         }
+        MGSA_TRACE(i, 10);
         sync_arrive<kBatch>(a.ctl, gen, s_flags);
         if (rest_prev)
           reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
+        MGSA_TRACE(i, 11);
         if (!sync_wait<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+        MGSA_TRACE(i, 12);
         zsrc = zi;
       } else {
         zsrc = Z;  // column 0 of the input equals the working column 0

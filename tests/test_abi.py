@@ -60,3 +60,19 @@ def test_create_without_gpu_fails_cleanly():
     st = mgsa.lib().mgsa_create(ctypes.byref(h), 0)
     assert st in (mgsa.MGSA_ERR_CUDA, mgsa.MGSA_ERR_INVALID)
     assert h.value is None
+
+
+def test_plain_c_client_builds_and_fails_cleanly_without_gpu(tmp_path):
+    """include/mgsa.h is a C11 header: a C program compiles against it with
+    -Wall -Wextra -Werror -pedantic, links libmgsa, and (without a GPU)
+    mgsa_create reports an error instead of crashing."""
+    import subprocess
+
+    import torch
+    from c_client import build_client
+
+    exe = build_client(str(tmp_path))
+    if torch.cuda.is_available():
+        return  # the GPU run is tests/test_gpu_c_client.py
+    r = subprocess.run([exe, "100", "4", "1"], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.startswith("nogpu"), (r.stdout, r.stderr)

@@ -130,6 +130,19 @@ size_t mgsa_workspace_bytes(mgsa_handle h, int64_t m, int n, mgsa_variant v);
 mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
                     mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, mgsa_stream_t s);
 
+/* Time-sliced mgsa_qr: run steps [first, first + count) of the loop (step i
+ * forms q_i and row i of R) as one launch, so that other work can run on the
+ * GPU between slices.  Calls with first = 0, 1 * count, 2 * count, ... up to n
+ * in order, on one stream, give bit for bit the results of one mgsa_qr call.
+ * The first slice (first == 0) reads Z; later ones continue from Q, R and the
+ * handle's workspace, so between the slices of one QR the handle must run no
+ * other QR and its parameters must not change.  A slice after a failed one
+ * does nothing; mgsa_get_info reports the failure.  MGS forms only
+ * (MGSA_NAIVE / MGSA_HA / MGSA_HP); arguments as for mgsa_qr. */
+mgsa_status mgsa_qr_steps(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
+                          mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, int first, int count,
+                          mgsa_stream_t s);
+
 /* Wait for stream s and report the outcome of the last mgsa_qr queued on h.
  * *info = 0 on success; otherwise the 1-based column j at which z_j^T x_j was
  * not positive (return MGSA_ERR_BREAKDOWN) or not finite (MGSA_ERR_NONFINITE),

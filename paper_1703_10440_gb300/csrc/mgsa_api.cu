@@ -271,7 +271,8 @@ mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value) {
 // (nullable) receives the p_j of the new columns.
 static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
                              mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, int kg, const double* Qg,
-                             int64_t ldqg, const double* Pg, int64_t ldpg, double* P, int64_t ldp, mgsa_stream_t s) {
+                             int64_t ldqg, const double* Pg, int64_t ldpg, double* P, int64_t ldp, mgsa_stream_t s,
+                             int step_begin = 0, int step_end = -1) {
   if (!h) return fail(MGSA_ERR_INVALID, "NULL handle");
   if (!A || !Z || !Q || !R) return fail(MGSA_ERR_INVALID, "NULL matrix pointer");
   if (kg < 0 || kg > MGSA_MAX_N - 1) return fail(MGSA_ERR_INVALID, "k must be in [0, MGSA_MAX_N)");
@@ -343,6 +344,8 @@ static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, 
     a.qp = a.X + p.ldx * p.xcols;
     a.stages = p.stages;
   }
+  a.step_begin = step_begin;
+  a.step_end = step_end;
   a.kg = kg;
   a.Qg = Qg;
   a.ldqg = ldqg;
@@ -357,7 +360,10 @@ static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, 
   }
 
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
-  cudaError_t e = cudaMemsetAsync(h->ctl, 0, sizeof(int) * mgsa::kCtlWords, cs);
+  // A first slice clears the whole control block; a later one only the
+  // barrier counters (the status word carries an earlier slice's failure).
+  cudaError_t e = step_begin == 0 ? cudaMemsetAsync(h->ctl, 0, sizeof(int) * mgsa::kCtlWords, cs)
+                                  : cudaMemsetAsync(h->ctl + mgsa::kCtlBarCount, 0, 2 * sizeof(int), cs);
   if (e != cudaSuccess) return cuda_fail(e);
   e = is_cgs(v) ? mgsa::cgs_launch(kernel_variant(v), a, p.grid, p.smem, cs)
                 : mgsa::sweep_launch(kernel_variant(v), a, p.grid, p.smem, cs);
@@ -368,6 +374,16 @@ static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, 
 mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
                     mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, mgsa_stream_t s) {
   return qr_launch(h, A, Z, m, n, ldz, v, Q, ldq, R, ldr, 0, nullptr, 0, nullptr, 0, nullptr, 0, s);
+}
+
+mgsa_status mgsa_qr_steps(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz,
+                          mgsa_variant v, double* Q, int64_t ldq, double* R, int ldr, int first, int count,
+                          mgsa_stream_t s) {
+  if (v != MGSA_NAIVE && v != MGSA_HA && v != MGSA_HP) return fail(MGSA_ERR_INVALID, "time slicing takes MGS forms only");
+  if (first < 0 || count < 1 || first >= n || count > n - first)
+    return fail(MGSA_ERR_INVALID, "steps [first, first + count) must lie in [0, n)");
+  return qr_launch(h, A, Z, m, n, ldz, v, Q, ldq, R, ldr, 0, nullptr, 0, nullptr, 0, nullptr, 0, s, first,
+                   first + count);
 }
 
 mgsa_status mgsa_qr_append(mgsa_handle h, const mgsa_csr* A, const double* Qold, int64_t ldqo, const double* Pold,

@@ -57,6 +57,12 @@ struct SweepArgs {
   // buffers of 2 * chunk doubles feed them to the update pass.
   double* qp = nullptr;
   int stages = 0;
+  // Time slicing: this launch runs steps [step_begin, step_end) of the loop
+  // (step_end < 0: to the end).  A slice that starts after step 0 reloads its
+  // pivots and R row step_begin - 1 from global memory; one that ends early
+  // sums its last R row in full.
+  int step_begin = 0;
+  int step_end = -1;
 };
 
 // Average row length from which a warp, not a thread, takes one CSR row.

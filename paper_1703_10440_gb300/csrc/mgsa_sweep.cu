@@ -192,8 +192,12 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
   auto qsrc = [&](int i) -> const double* { return i < kg ? a.Qg + (int64_t)i * a.ldqg : zcol(i); };
   auto psrc = [&](int i) -> const double* { return i < kg ? a.Pg + (int64_t)i * a.ldpg : xcol(i); };
   unsigned int gen = 0;
+  // Steps [i0, i1) run in this launch (time slicing; the whole loop by default).
+  const int i0 = a.step_begin;
+  const int i1 = (a.step_end < 0 || a.step_end > nt) ? nt : a.step_end;
 
   MGSA_TRACE(4100, 0);
+  if (i0 == 0) {
   // ---- Phase 0: R = 0; Q = Z on own rows; HP: X = A Z (one block product,
   // Algorithm 8 first line) and, outside resident mode, the partial z_1^T x_1. ----
   if (b == 0) {
@@ -209,10 +213,29 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     for (int j = 0; j < n; ++j)
       for (int64_t k = k0 + tid; k < k1; k += kThreads) Q[k + (int64_t)j * ldq] = __ldg(Z + k + (int64_t)j * ldz);
   }
+  } else {
+    // ---- A later slice: stop if an earlier one failed (the status word
+    // survives between slices; no CTA writes it before the first wait, so
+    // every CTA reads the same value).  Otherwise reload what the previous
+    // slice left: R row i0-1 (summed in full at its end) and, in resident
+    // mode, the pivots q_{i0-1} (Q) and p_{i0-1} (HP: X). ----
+    if (ld_relaxed_i32(&a.ctl[kCtlStatus]) != 0) return 0;
+    for (int j = i0 + tid; j < nt; j += kThreads) s_rrow[j] = ld_cg(R + (i0 - 1) + (int64_t)(j - kg) * ldr);
+    if (resident) {
+      double* sq = s_piv + 2 * ((i0 - 1) & 1) * chunk;
+      const double* qg = qsrc(i0 - 1) + k0;
+      const double* pg = psrc(i0 - 1) + k0;
+      const int nb32 = ((crows_all + 31) >> 5) * 32;
+      for (int r = tid; r < nb32; r += kThreads) {
+        sq[r] = r < crows_all ? ld_cg(qg + r) : 0.0;
+        if (V == kHP) sq[chunk + r] = r < crows_all ? ld_cg(pg + r) : 0.0;
+      }
+    }
+  }
   __syncthreads();
   MGSA_TRACE(4100, 1);
 
-  for (int i = 0; i < nt; ++i) {
+  for (int i = i0; i < i1; ++i) {
     MGSA_TRACE(i, 0);
     const int cur = i & 1, prev = cur ^ 1;
     const bool given = i < kg;  // pivot q_i, p_i given (successive orthogonalisation)
@@ -220,8 +243,9 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     const double* part_prev = a.part + (int64_t)prev * nt * G;  // partials of row i-1
     double* part_cur = a.part + (int64_t)cur * nt * G;          // partials of row i
     // The rest of row i-1 is summed during this step's first wait, unless row
-    // i-1 was a given step's (summed in full right away).
-    const bool rest_prev = i > kg;
+    // i-1 was a given step's or the last of the previous slice (summed in full
+    // right away).
+    const bool rest_prev = i > kg && i > i0;
     // This thread's rows tid + t*kThreads of z_i and x_i (naive: p_i), resident mode only.
     double zr[kResRows], xr[kResRows];
     // ---------------- column i: r_ii = sqrt(z_i^T x_i) ----------------
@@ -564,6 +588,10 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       reduce_range(part_cur, G, nt, jbeg, nt, s_rrow, s_buf, b == 0 ? R + i : nullptr, ldr, kg);  // all of row i
     } else {
       reduce_first(part_cur, G, nt, i, s_rrow, R, ldr, kg, b == 0);  // r_{i,i+1}; the rest at the next wait
+      // The last step of a slice sums the rest of row i now, with the same
+      // trees as the next step's wait would, for the next slice to reload.
+      if (i + 1 == i1)
+        reduce_range(part_cur, G, nt, i + 2, nt, s_rrow, s_buf, b == 0 ? R + i : nullptr, ldr, kg);
     }
     MGSA_TRACE(i, 9);
   }

@@ -67,6 +67,8 @@ SIGNATURES = {
     "mgsa_reserve": (_INT, [_VP, _I64, _INT, _INT]),
     "mgsa_workspace_bytes": (_SZ, [_VP, _I64, _INT, _INT]),
     "mgsa_qr": (_INT, [_VP, ctypes.POINTER(mgsa_csr), _VP, _I64, _INT, _I64, _INT, _VP, _I64, _VP, _INT, _VP]),
+    "mgsa_qr_steps": (_INT, [_VP, ctypes.POINTER(mgsa_csr), _VP, _I64, _INT, _I64, _INT, _VP, _I64, _VP, _INT, _INT,
+                             _INT, _VP]),
     "mgsa_get_info": (_INT, [_VP, _VP, ctypes.POINTER(_INT)]),
     "mgsa_copy_info": (_INT, [_VP, _VP, _VP]),
     "mgsa_qr_host": (_INT, [_VP, _VP, _VP, _VP, _I64, _VP, _I64, _INT, _I64, _INT, _VP, _I64, _VP, _INT, _VP,
@@ -170,6 +172,13 @@ def mgsa_qr_append(h: int, A: mgsa_csr, Qold, ldqo: int, Pold, ldpo: int, k: int
     returns the status of the call.  ``P`` may be None."""
     return int(lib().mgsa_qr_append(h, ctypes.byref(A), _ptr(Qold), ldqo, _ptr(Pold), ldpo, k, _ptr(Z), m, n, ldz,
                                     variant, _ptr(Q), ldq, _ptr(P), ldp, _ptr(R), ldr, _stream(stream)))
+
+
+def mgsa_qr_steps(h: int, A: mgsa_csr, Z, m: int, n: int, ldz: int, variant: int, Q, ldq: int, R, ldr: int,
+                  first: int, count: int, stream=None) -> int:
+    """Queue steps [first, first + count) of a time-sliced QR; returns the status of the call."""
+    return int(lib().mgsa_qr_steps(h, ctypes.byref(A), _ptr(Z), m, n, ldz, variant, _ptr(Q), ldq, _ptr(R), ldr, first,
+                                   count, _stream(stream)))
 
 
 def mgsa_qr_noalloc(A: mgsa_csr, Z, m: int, n: int, ldz: int, variant: int, Q, ldq: int, R, ldr: int, info_dev=None,

@@ -492,7 +492,8 @@ def run_served(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     h = mgsa.Handle(local_rank)
     srv = Server(h.h, args.serve_variant, budget_bytes=120e9, small_work=args.serve_small_work, device=local_rank,
-                 small_ctas=args.serve_small_ctas, max_large_inflight=args.serve_large_window)
+                 small_ctas=args.serve_small_ctas, max_large_inflight=args.serve_large_window,
+                 slice_ms=args.serve_slice_ms)
     rates = [float(x) for x in args.serve_sweep.split(",")] if args.serve_sweep else [args.serve_rate]
     streams = {rate: poisson_arrivals(rate, args.serve_seconds, seed=W.SEED + rank) for rate in rates}
     warm = streams[rates[0]][:4]
@@ -542,7 +543,7 @@ def run_served(args, rank, world, local_rank):
             "config": {"workload": "served_poisson_m1e3-1e6_n8-128_laplace/banded", "rate_per_s": main["rate_per_s"],
                        "seconds": args.serve_seconds, "requests": main["requests"], "variant": args.serve_variant,
                        "budget_gb": 120, "small_work": args.serve_small_work, "small_ctas": args.serve_small_ctas,
-                       "large_window": args.serve_large_window},
+                       "large_window": args.serve_large_window, "slice_ms": args.serve_slice_ms},
             "served": {"sweep": sweep, "solo_p50_ms": float(np.median(solo_s) * 1e3), "solo_p99_ms": solo_p99_ms,
                        "solo_serial_qr_per_s": serial_qr_per_s,
                        "served_over_serial": main["qr_per_s"] / serial_qr_per_s,
@@ -568,8 +569,10 @@ def main():
     ap.add_argument("--serve-sample", type=int, default=200, help="served: requests per rate timed alone as well")
     ap.add_argument("--serve-small-ctas", type=int, default=16,
                     help="served: SMs kept for small requests (0 = no partition)")
-    ap.add_argument("--serve-large-window", type=int, default=2,
+    ap.add_argument("--serve-large-window", type=int, default=1,
                     help="served: large launches kept in flight, least work first (0 = all, in arrival order)")
+    ap.add_argument("--serve-slice-ms", type=float, default=2.0,
+                    help="served: time slices of about this long for large requests (0 = whole QRs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

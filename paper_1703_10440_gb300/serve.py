@@ -13,6 +13,11 @@ that asks for many A-orthonormalisations of different sizes.  The server:
 * with ``max_large_inflight`` = w > 0, keeps at most w large launches queued
   on the device and launches the waiting large request with the least work
   (m * n^2) next, so medium requests overtake queued big ones;
+* with ``slice_ms`` > 0, runs large requests in time slices of about that
+  long (``mgsa_qr_steps``), each request on a handle of its own from a small
+  pool, and picks the slice to launch next by least remaining work, so a
+  request that arrives while a long factorisation runs waits for one slice,
+  not for the whole factorisation;
 * with ``small_ctas`` = k > 0, partitions the SMs: large requests run with
   k fewer CTAs than the GPU has SMs, small ones on a second stream and a
   second handle whose batched launches use k CTAs, so the two kinds run side
@@ -59,6 +64,9 @@ class Request:
     t_done: float = math.nan
     info: int = -99
     info_buf: object = None
+    handle: int = 0          # sliced large requests: the pool handle holding its state
+    next_step: int = 0       # sliced large requests: first step of the next slice
+    slice_inflight: bool = False
 
 
 def poisson_arrivals(rate: float, duration: float, seed: int = 20170330, m_lo: float = 1e3, m_hi: float = 1e6,
@@ -84,7 +92,7 @@ def poisson_arrivals(rate: float, duration: float, seed: int = 20170330, m_lo: f
 class Server:
     def __init__(self, handle: int, variant: str = "hp", budget_bytes: float = 120e9, small_work: float = 2e7,
                  device: int = 0, max_batch: int = 4096, max_m: int = 1_000_000, max_n: int = 128,
-                 small_ctas: int = 0, max_large_inflight: int = 0):
+                 small_ctas: int = 0, max_large_inflight: int = 0, slice_ms: float = 0.0, large_handles: int = 3):
         import torch
 
         self.torch = torch
@@ -112,15 +120,74 @@ class Server:
         # Large requests share the handle's workspace: size it once, up front.
         mgsa.mgsa_reserve(handle, max_m, max_n, self.v)
         self.shared_ws = mgsa.mgsa_workspace_bytes(handle, max_m, max_n, self.v)
+        # Sliced large requests: one pool handle per request in progress.
+        self.slice_ms = slice_ms
+        self._pool: list[int] = []
+        if slice_ms > 0:
+            sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
+            for _ in range(large_handles):
+                hh = mgsa.mgsa_create(device)
+                if small_ctas > 0:
+                    mgsa.mgsa_set_param(hh, mgsa.MGSA_PARAM_MAX_CTAS, sms - small_ctas)
+                mgsa.mgsa_reserve(hh, max_m, max_n, self.v)
+                self._pool.append(hh)
+            self.shared_ws += large_handles * mgsa.mgsa_workspace_bytes(self._pool[0], max_m, max_n, self.v)
+        self._all_pool = list(self._pool)
 
     def close(self):
-        """Undo the SM partition (the caller's handle gets its default CTA count back)."""
+        """Undo the SM partition (the caller's handle gets its default CTA
+        count back) and release the handles the server created."""
+        self.torch.cuda.synchronize(self.dev)
         if self._own_handle:
-            self.torch.cuda.synchronize(self.dev)
             mgsa.mgsa_set_param(self.h, mgsa.MGSA_PARAM_MAX_CTAS, 0)
             mgsa.mgsa_destroy(self._own_handle)
             self._own_handle = 0
             self.h_small = self.h
+        for hh in self._all_pool:
+            mgsa.mgsa_destroy(hh)
+        self._all_pool, self._pool = [], []
+
+    # -- time slices of large requests --------------------------------------
+    # Cost model of one step (seconds): the sweep's FP64 work on the remaining
+    # columns at an effective 0.8 TFLOP/s, the per-column MVs of HA / naive,
+    # and a fixed 20 us of barriers and reductions.
+    def _step_s(self, r: Request, i: int) -> float:
+        per_pair = 6.0 if self.variant == "hp" else 4.0
+        nnz_row = 5.0 if r.kind == "laplace" else 17.0
+        mvs = 0 if self.variant == "hp" else (2 if self.variant == "naive" else 1)
+        return (per_pair * r.m * (r.n - 1 - i) + mvs * 2.0 * nnz_row * r.m) / 0.8e12 + 20e-6
+
+    def _remaining_s(self, r: Request) -> float:
+        k = r.n - r.next_step
+        per_pair = 6.0 if self.variant == "hp" else 4.0
+        nnz_row = 5.0 if r.kind == "laplace" else 17.0
+        mvs = 0 if self.variant == "hp" else (2 if self.variant == "naive" else 1)
+        return (per_pair * r.m * k * (k - 1) / 2 + mvs * 2.0 * nnz_row * r.m * k) / 0.8e12 + 20e-6 * k
+
+    def _launch_slice(self, r: Request):
+        torch = self.torch
+        if r.next_step == 0:  # its inputs come from the generator stream
+            ready = torch.cuda.Event()
+            ready.record(self.gen_stream)
+            self.stream.wait_event(ready)
+        first, count, t = r.next_step, 0, 0.0
+        while first + count < r.n and (count == 0 or t < self.slice_ms * 1e-3):
+            t += self._step_s(r, first + count)
+            count += 1
+        rowptr, col, val = r.A
+        csr = mgsa.make_csr(r.m, col.numel(), rowptr, col, val)
+        st = mgsa.mgsa_qr_steps(r.handle, csr, r.Z, r.m, r.n, r.m, self.v, r.Q, r.Q.stride(0), r.R, r.n, first, count,
+                                self.stream)
+        if st != mgsa.MGSA_OK:
+            raise mgsa.MgsaError(st, mgsa.mgsa_last_error())
+        r.next_step = first + count
+        last = r.next_step >= r.n
+        if last:
+            mgsa.mgsa_copy_info(r.handle, r.info_buf, self.stream)
+        done = torch.cuda.Event(enable_timing=True)
+        done.record(self.stream)
+        r.slice_inflight = True
+        return ("slice", [r], done, last)
 
     # -- admission ---------------------------------------------------------
     def _bytes(self, r: Request) -> int:
@@ -198,7 +265,8 @@ class Server:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting: collections.deque = collections.deque()
         inflight: collections.deque = collections.deque()
-        ready_large: list = []  # admitted large requests not yet launched (max_large_inflight > 0)
+        ready_large: list = []  # admitted large requests not yet launched (max_large_inflight > 0 or slicing)
+        running: list = []      # sliced large requests with slices still to run
         used = self.shared_ws
         peak = used
         torch.cuda.synchronize(self.dev)
@@ -207,14 +275,15 @@ class Server:
         ref.synchronize()
         t0 = time.perf_counter()
         ticks = launches = 0
-        while pending or waiting or inflight or ready_large:
+        window = self.max_large_inflight if self.max_large_inflight > 0 else 2
+        while pending or waiting or inflight or ready_large or running:
             now = time.perf_counter() - t0
             while pending and (not realtime or pending[0].arrival <= now):
                 waiting.append(pending.popleft())
             admitted = []
             while waiting and len(admitted) < self.max_batch:
                 need = self._bytes(waiting[0])
-                if used + need > self.budget and (inflight or admitted or ready_large):
+                if used + need > self.budget and (inflight or admitted or ready_large or running):
                     break
                 r = waiting.popleft()
                 self._materialize(r)
@@ -223,7 +292,25 @@ class Server:
                 admitted.append(r)
             peak = max(peak, used)
             launch_now = admitted
-            if self.max_large_inflight > 0:
+            if self.slice_ms > 0:
+                ready_large.extend(r for r in admitted if not r.small)
+                launch_now = [r for r in admitted if r.small]
+                n_slices = sum(1 for grp in inflight if grp[0] == "slice")
+                while n_slices < window:
+                    cands = [r for r in running if not r.slice_inflight]
+                    if self._pool:
+                        cands += ready_large
+                    if not cands:
+                        break
+                    nxt = min(cands, key=lambda r: (self._remaining_s(r), r.arrival))
+                    if nxt.next_step == 0 and nxt in ready_large:
+                        ready_large.remove(nxt)
+                        nxt.handle = self._pool.pop()
+                        running.append(nxt)
+                    inflight.append(self._launch_slice(nxt))
+                    launches += 1
+                    n_slices += 1
+            elif self.max_large_inflight > 0:
                 ready_large.extend(r for r in admitted if not r.small)
                 launch_now = [r for r in admitted if r.small]
                 n_large = sum(1 for grp in inflight if grp[0] == "single")
@@ -243,7 +330,17 @@ class Server:
                 inflight = collections.deque(grp for grp in inflight if not any(grp is f for f in finished))
             for kind, reqs, done, extra in finished:
                 t_done = ref.elapsed_time(done) / 1e3
-                if kind == "batch":
+                if kind == "slice":
+                    r = reqs[0]
+                    r.slice_inflight = False
+                    progressed = True
+                    if not extra:  # more slices to come
+                        continue
+                    running.remove(r)
+                    self._pool.append(r.handle)
+                    r.handle = 0
+                    infos = [int(r.info_buf[0].item())]
+                elif kind == "batch":
                     infos = extra[1].cpu().numpy()
                 else:
                     infos = [int(reqs[0].info_buf[0].item())]

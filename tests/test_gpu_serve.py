@@ -142,3 +142,29 @@ def test_shortest_work_first_window(handle):
         Q, R, _ = srv.results[r.rid]
         Qp, Rp, _ = plain.results[r.rid]
         assert np.array_equal(Q, Qp) and np.array_equal(R, Rp)
+
+
+@pytest.mark.parametrize("variant", ["ha", "hp"])
+def test_time_sliced_large_requests(handle, variant):
+    """slice_ms: large requests run as time slices on pool handles, least
+    remaining work first; every result is bitwise that of the unsliced
+    server with the same SM partition."""
+    reqs = make_requests()
+    kw = dict(budget_bytes=8e9, small_work=5e6, max_m=60000, max_n=48, small_ctas=16)
+    sl = KeepingServer(handle.h, variant, slice_ms=0.05, large_handles=2, **kw)
+    try:
+        stats = sl.run(fresh(reqs), realtime=True)
+    finally:
+        sl.close()
+    assert stats["ok"] == len(reqs)
+    assert stats["launches"] > stats["small"] and 0 < stats["small"] < len(reqs)
+    plain = KeepingServer(handle.h, variant, **kw)
+    try:
+        plain.run(fresh(reqs), realtime=False)
+    finally:
+        plain.close()
+    for r in reqs:
+        Q, R, info = sl.results[r.rid]
+        Qp, Rp, infop = plain.results[r.rid]
+        assert info == infop == 0
+        assert np.array_equal(Q, Qp) and np.array_equal(R, Rp), r.rid

@@ -569,7 +569,7 @@ def main():
     ap.add_argument("--serve-sample", type=int, default=200, help="served: requests per rate timed alone as well")
     ap.add_argument("--serve-small-ctas", type=int, default=16,
                     help="served: SMs kept for small requests (0 = no partition)")
-    ap.add_argument("--serve-large-window", type=int, default=1,
+    ap.add_argument("--serve-large-window", type=int, default=2,
                     help="served: large launches kept in flight, least work first (0 = all, in arrival order)")
     ap.add_argument("--serve-slice-ms", type=float, default=2.0,
                     help="served: time slices of about this long for large requests (0 = whole QRs)")

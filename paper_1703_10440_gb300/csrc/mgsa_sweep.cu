@@ -150,7 +150,9 @@ __device__ __forceinline__ void fused_pass(int i, int jbeg, int ncols, int kg, i
 
 // The whole right-looking loop for one instance, run by G CTAs (CTA b owns
 // rows [b*rpc, (b+1)*rpc)).  Returns 0 or body_result(status, column).
-template <int V, bool kBatch, int kPanel>
+// kSliced: the launch may be one time slice of the loop (steps [step_begin,
+// step_end)); otherwise the whole loop, and none of the slicing code exists.
+template <int V, bool kBatch, int kPanel, bool kSliced>
 __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* smem, int* s_wfirst, int* s_wlast,
                           int* s_flags) {
   const int n = a.n;    // columns of Z
@@ -193,11 +195,11 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
   auto psrc = [&](int i) -> const double* { return i < kg ? a.Pg + (int64_t)i * a.ldpg : xcol(i); };
   unsigned int gen = 0;
   // Steps [i0, i1) run in this launch (time slicing; the whole loop by default).
-  const int i0 = a.step_begin;
-  const int i1 = (a.step_end < 0 || a.step_end > nt) ? nt : a.step_end;
+  const int i0 = kSliced ? a.step_begin : 0;
+  const int i1 = (!kSliced || a.step_end < 0 || a.step_end > nt) ? nt : a.step_end;
 
   MGSA_TRACE(4100, 0);
-  if (i0 == 0) {
+  if (!kSliced || i0 == 0) {
   // ---- Phase 0: R = 0; Q = Z on own rows; HP: X = A Z (one block product,
   // Algorithm 8 first line) and, outside resident mode, the partial z_1^T x_1. ----
   if (b == 0) {
@@ -245,7 +247,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     // The rest of row i-1 is summed during this step's first wait, unless row
     // i-1 was a given step's or the last of the previous slice (summed in full
     // right away).
-    const bool rest_prev = i > kg && i > i0;
+    const bool rest_prev = i > kg && (!kSliced || i > i0);
     // This thread's rows tid + t*kThreads of z_i and x_i (naive: p_i), resident mode only.
     double zr[kResRows], xr[kResRows];
     // ---------------- column i: r_ii = sqrt(z_i^T x_i) ----------------
@@ -590,7 +592,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       reduce_first(part_cur, G, nt, i, s_rrow, R, ldr, kg, b == 0);  // r_{i,i+1}; the rest at the next wait
       // The last step of a slice sums the rest of row i now, with the same
       // trees as the next step's wait would, for the next slice to reload.
-      if (i + 1 == i1)
+      if (kSliced && i + 1 == i1)
         reduce_range(part_cur, G, nt, i + 2, nt, s_rrow, s_buf, b == 0 ? R + i : nullptr, ldr, kg);
     }
     MGSA_TRACE(i, 9);
@@ -600,12 +602,12 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
 
 // Single instance over the whole grid (cooperative launch).
 // kPanel: columns per pass of the block product (HP; one instantiation per width).
-template <int V, int kPanel>
+template <int V, int kPanel, bool kSliced>
 __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(16) double smem[];
   __shared__ int s_wfirst[kWarps], s_wlast[kWarps];
   __shared__ int s_flags[2];
-  const int r = sweep_body<V, false, kPanel>(a, gridDim.x, blockIdx.x, smem, s_wfirst, s_wlast, s_flags);
+  const int r = sweep_body<V, false, kPanel, kSliced>(a, gridDim.x, blockIdx.x, smem, s_wfirst, s_wlast, s_flags);
   // Breakdown verdicts are identical in every CTA; CTA 0 records them.  A
   // timeout was recorded by the CTA that saw it.
   if (r != 0 && (r >> 24) != kDevTimeout && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.ctl, r >> 24, r & 0xFFFFFF);
@@ -657,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_batch_kernel(const BatchArgs 
       a.rpc = (m + 31) / 32 * 32;
       a.chunk = (int)(a.rpc < kMaxChunk ? a.rpc : kMaxChunk);
       a.mv_warp = ba.row_mode == 0 ? (int64_t)__ldg(J.rowptr + m) >= (int64_t)kWarpRowNnz * m : ba.row_mode == 2;
-      result = sweep_body<V, true, kPanel>(a, 1, 0, smem, s_wfirst, s_wlast, s_flags);
+      result = sweep_body<V, true, kPanel, false>(a, 1, 0, smem, s_wfirst, s_wlast, s_flags);
     }
     if (threadIdx.x == 0) {
       int info = 0;
@@ -672,15 +674,21 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_batch_kernel(const BatchArgs 
 
 }  // namespace
 
-// The kernels: naive and HA have no block product; HP has one per panel width.
-static const void* sweep_fn(int variant, int panel = 8) {
+// The kernels: naive and HA have no block product; HP has one per panel
+// width; each also as a time-slice instance.
+template <bool kSliced>
+static const void* sweep_fn_s(int variant, int panel) {
   switch (variant) {
-    case kNaive: return reinterpret_cast<const void*>(mgs_sweep_kernel<kNaive, 8>);
-    case kHA: return reinterpret_cast<const void*>(mgs_sweep_kernel<kHA, 8>);
+    case kNaive: return reinterpret_cast<const void*>(mgs_sweep_kernel<kNaive, 8, kSliced>);
+    case kHA: return reinterpret_cast<const void*>(mgs_sweep_kernel<kHA, 8, kSliced>);
     default:
-      return panel == 4 ? reinterpret_cast<const void*>(mgs_sweep_kernel<kHP, 4>)
-                        : reinterpret_cast<const void*>(mgs_sweep_kernel<kHP, 8>);
+      return panel == 4 ? reinterpret_cast<const void*>(mgs_sweep_kernel<kHP, 4, kSliced>)
+                        : reinterpret_cast<const void*>(mgs_sweep_kernel<kHP, 8, kSliced>);
   }
+}
+
+static const void* sweep_fn(int variant, int panel = 8, bool sliced = false) {
+  return sliced ? sweep_fn_s<true>(variant, panel) : sweep_fn_s<false>(variant, panel);
 }
 
 static const void* batch_fn(int variant, int panel = 8) {
@@ -701,11 +709,13 @@ cudaError_t sweep_prepare(int device) {
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e != cudaSuccess) return e;
   for (const auto& k : kKernelInstances) {
-    const void* fn = sweep_fn(k[0], k[1]);
-    cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
-    const int dyn = optin - (int)fa.sharedSizeBytes;  // static shared memory counts against the opt-in limit
-    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+    for (const bool sliced : {false, true}) {
+      const void* fn = sweep_fn(k[0], k[1], sliced);
+      cudaFuncAttributes fa;
+      if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+      const int dyn = optin - (int)fa.sharedSizeBytes;  // static shared memory counts against the opt-in limit
+      if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
@@ -756,7 +766,9 @@ cudaError_t batch_launch(const BatchArgs& ba, int grid, size_t smem, cudaStream_
 cudaError_t sweep_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s) {
   SweepArgs copy = a;
   void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel(sweep_fn(variant, a.spmm_panel), dim3(grid), dim3(kThreads), args, smem, s);
+  const bool sliced = a.step_begin != 0 || a.step_end >= 0;
+  return cudaLaunchCooperativeKernel(sweep_fn(variant, a.spmm_panel, sliced), dim3(grid), dim3(kThreads), args, smem,
+                                     s);
 }
 
 }  // namespace mgsa

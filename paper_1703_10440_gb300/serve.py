@@ -296,7 +296,12 @@ class Server:
                 ready_large.extend(r for r in admitted if not r.small)
                 launch_now = [r for r in admitted if r.small]
                 n_slices = sum(1 for grp in inflight if grp[0] == "slice")
-                while n_slices < window:
+                # One slice in flight keeps an arriving request's wait to one
+                # slice; with a backlog of large requests (four or more
+                # waiting), two keep the GPU busy while the host notices a
+                # completion.
+                slice_window = window if len(ready_large) >= 4 else min(window, 1)
+                while n_slices < slice_window:
                     cands = [r for r in running if not r.slice_inflight]
                     if self._pool:
                         cands += ready_large

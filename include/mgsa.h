@@ -133,7 +133,8 @@ mgsa_status mgsa_qr(mgsa_handle h, const mgsa_csr* A, const double* Z, int64_t m
 /* Time-sliced mgsa_qr: run steps [first, first + count) of the loop (step i
  * forms q_i and row i of R) as one launch, so that other work can run on the
  * GPU between slices.  Calls with first = 0, 1 * count, 2 * count, ... up to n
- * in order, on one stream, give bit for bit the results of one mgsa_qr call.
+ * in order, on one stream, give bit for bit the results of one mgsa_qr call
+ * on the whole GPU (slices never use a cluster: MGSA_PARAM_CLUSTER = 1).
  * The first slice (first == 0) reads Z; later ones continue from Q, R and the
  * handle's workspace, so between the slices of one QR the handle must run no
  * other QR and its parameters must not change.  A slice after a failed one
@@ -269,12 +270,21 @@ mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, 
  *                                >= 32 nonzeros per row, else one thread per
  *                                row (default); 1 = one thread per row (32 rows
  *                                per warp); 2 = one warp per row
+ *   MGSA_PARAM_CLUSTER           0 = automatic (default): a QR small enough
+ *                                (at most 256 rows per CTA of the largest
+ *                                cluster the GPU takes, and m * n <= 2^18)
+ *                                runs on one thread-block cluster of up to 16
+ *                                CTAs with hardware cluster barriers instead
+ *                                of the whole GPU; 1 = never;
+ *                                2..16 = always, on a cluster of that many CTAs
+ *                                (MGSA_ERR_INVALID from mgsa_qr if the GPU
+ *                                cannot co-schedule it).  MGS forms only.
  *   MGSA_PARAM_SPMM_PANEL        columns of Z per pass over A in the block
  *                                product X = A Z (HP): 4 or 8 (0 = 8), each
  *                                width a kernel of its own; every column's
  *                                sums are the same for either width
  * Results stay deterministic for a fixed setting; different MAX_CTAS,
- * CHUNK_ROWS, MIN_ROWS_PER_CTA or ROW_MODE settings change the reduction
+ * CHUNK_ROWS, MIN_ROWS_PER_CTA, ROW_MODE or CLUSTER settings change the reduction
  * tree and therefore the last bits of Q and R (BATCH_CTAS and SPMM_PANEL do
  * not).  The settings of a handle apply to its mgsa_qr, mgsa_qr_append and
  * (ROW_MODE, SPMM_PANEL, BATCH_CTAS) mgsa_qr_batched calls.  Returns MGSA_ERR_INVALID for an unknown parameter or an
@@ -285,7 +295,8 @@ typedef enum {
   MGSA_PARAM_MIN_ROWS_PER_CTA = 2,
   MGSA_PARAM_BATCH_CTAS = 3,
   MGSA_PARAM_ROW_MODE = 4,
-  MGSA_PARAM_SPMM_PANEL = 5
+  MGSA_PARAM_SPMM_PANEL = 5,
+  MGSA_PARAM_CLUSTER = 6
 } mgsa_param;
 mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value);
 

@@ -114,16 +114,34 @@ __device__ __forceinline__ bool grid_sync(int* ctl, unsigned int& gen, int* s_fl
   return grid_wait(ctl, gen, s_flags, s_flags + 1);
 }
 
+// Hardware barrier of a thread-block cluster: every thread of every CTA of
+// the cluster arrives (release) and waits (acquire), so the memory writes
+// before it are visible to the whole cluster after it.  No spinning: the
+// hardware holds the warps.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 // Synchronisation of the step body: device-wide for the single-instance
-// kernel, CTA-wide when one CTA owns a whole instance (batched kernel).
-template <bool kBatch>
+// kernel, CTA-wide when one CTA owns a whole instance (batched kernel),
+// cluster-wide when one thread-block cluster owns it (kCluster).
+// The cluster form keeps the CTA barrier in front of the arrive, as
+// grid_arrive does: the work between arrive and wait may reuse shared buffers
+// that other threads of the CTA read just before.
+template <bool kBatch, bool kCluster = false>
 __device__ __forceinline__ void sync_arrive(int* ctl, unsigned int gen, int* s_flags) {
-  if (kBatch) __syncthreads();
+  if (kCluster) {
+    __syncthreads();
+    cluster_arrive();
+  } else if (kBatch) __syncthreads();
   else grid_arrive(ctl, gen, s_flags);
 }
 
-template <bool kBatch>
+template <bool kBatch, bool kCluster = false>
 __device__ __forceinline__ bool sync_wait(int* ctl, unsigned int& gen, int* s_flags) {
+  if (kCluster) {
+    cluster_wait();
+    return true;
+  }
   if (kBatch) {
     __syncthreads();
     return true;
@@ -131,10 +149,10 @@ __device__ __forceinline__ bool sync_wait(int* ctl, unsigned int& gen, int* s_fl
   return grid_wait(ctl, gen, s_flags, s_flags + 1);
 }
 
-template <bool kBatch>
+template <bool kBatch, bool kCluster = false>
 __device__ __forceinline__ bool sync_all(int* ctl, unsigned int& gen, int* s_flags) {
-  sync_arrive<kBatch>(ctl, gen, s_flags);
-  return sync_wait<kBatch>(ctl, gen, s_flags);
+  sync_arrive<kBatch, kCluster>(ctl, gen, s_flags);
+  return sync_wait<kBatch, kCluster>(ctl, gen, s_flags);
 }
 
 // Result of the step body: 0, or (device status << 24) | 1-based column.

@@ -114,6 +114,13 @@ cudaError_t sweep_prepare(int device);  // sets shared-memory attributes once pe
 cudaError_t sweep_max_ctas(int variant, size_t smem, int* max_ctas);
 cudaError_t sweep_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s);
 
+// One instance on one thread-block cluster of up to kMaxClusterCtas CTAs
+// (non-portable sizes above 8 allowed where the GPU takes them).
+constexpr int kMaxClusterCtas = 16;
+cudaError_t cluster_prepare(int device);
+cudaError_t cluster_max_size(int variant, size_t smem, int* max_size);
+cudaError_t cluster_launch(int variant, const SweepArgs& a, int ctas, size_t smem, cudaStream_t s);
+
 // Left-looking CGS kernels (mgsa_cgs.cu); variant = kNaive / kHA / kHP.
 // X holds n columns (HP: x_j) or 2 (HA, naive: z_j, x_j); qp as in SweepArgs.
 // cgs_smem_plan picks the number of pivot buffers that fit next to the rest.

@@ -152,7 +152,7 @@ __device__ __forceinline__ void fused_pass(int i, int jbeg, int ncols, int kg, i
 // rows [b*rpc, (b+1)*rpc)).  Returns 0 or body_result(status, column).
 // kSliced: the launch may be one time slice of the loop (steps [step_begin,
 // step_end)); otherwise the whole loop, and none of the slicing code exists.
-template <int V, bool kBatch, int kPanel, bool kSliced>
+template <int V, bool kBatch, int kPanel, bool kSliced, bool kCluster = false>
 __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* smem, int* s_wfirst, int* s_wlast,
                           int* s_flags) {
   const int n = a.n;    // columns of Z
@@ -313,10 +313,10 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         if (tid == 0) part_norm[b] = sl;
       }
       MGSA_TRACE(i, 1);
-      sync_arrive<kBatch>(a.ctl, gen, s_flags);
+      sync_arrive<kBatch, kCluster>(a.ctl, gen, s_flags);
       if (rest_prev)  // r_{i-1,j}, j > i
         reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
-      if (!sync_wait<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+      if (!sync_wait<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     } else {
       const double* zsrc;  // column i of the working Z, complete on every row
       if (i > 0) {
@@ -354,11 +354,11 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
           }
         }
         MGSA_TRACE(i, 10);
-        sync_arrive<kBatch>(a.ctl, gen, s_flags);
+        sync_arrive<kBatch, kCluster>(a.ctl, gen, s_flags);
         if (rest_prev)
           reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
         MGSA_TRACE(i, 11);
-        if (!sync_wait<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+        if (!sync_wait<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
         MGSA_TRACE(i, 12);
         zsrc = zi;
       } else {
@@ -432,7 +432,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       sl = block_sum(sl, s_buf);
       if (tid == 0) part_norm[b] = sl;
       MGSA_TRACE(i, 1);
-      if (!sync_all<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+      if (!sync_all<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     }
     MGSA_TRACE(i, 2);
     diagonal(part_norm, G, s_scal);
@@ -482,7 +482,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         }
       }
       // Other CTAs still gather z_i; q_i may overwrite it only after this wait.
-      if (!sync_all<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+      if (!sync_all<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     }
     }  // !given
 
@@ -584,7 +584,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     if (ncols == 0) break;
     for (int jr = tid; jr < ncols; jr += kThreads) part_cur[(int64_t)b * nt + (jbeg + jr)] = s_racc[jr];
     MGSA_TRACE(i, 7);
-    if (!sync_all<kBatch>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+    if (!sync_all<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     MGSA_TRACE(i, 8);
     if (given) {
       reduce_range(part_cur, G, nt, jbeg, nt, s_rrow, s_buf, b == 0 ? R + i : nullptr, ldr, kg);  // all of row i
@@ -611,6 +611,19 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
   // Breakdown verdicts are identical in every CTA; CTA 0 records them.  A
   // timeout was recorded by the CTA that saw it.
   if (r != 0 && (r >> 24) != kDevTimeout && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.ctl, r >> 24, r & 0xFFFFFF);
+}
+
+// Single instance on one thread-block cluster (the whole grid): the same loop
+// with hardware cluster barriers instead of the device-wide ones.  For
+// problems too small to keep the whole GPU busy, where the per-step barrier
+// latency, not the arithmetic, sets the time.
+template <int V, int kPanel>
+__global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(const SweepArgs a) {
+  extern __shared__ __align__(16) double smem[];
+  __shared__ int s_wfirst[kWarps], s_wlast[kWarps];
+  __shared__ int s_flags[2];
+  const int r = sweep_body<V, false, kPanel, false, true>(a, gridDim.x, blockIdx.x, smem, s_wfirst, s_wlast, s_flags);
+  if (r != 0 && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.ctl, r >> 24, r & 0xFFFFFF);
 }
 
 // Many independent instances: every CTA takes the next job from the queue and
@@ -718,6 +731,69 @@ cudaError_t sweep_prepare(int device) {
     }
   }
   return cudaSuccess;
+}
+
+static const void* cluster_fn(int variant, int panel = 8) {
+  switch (variant) {
+    case kNaive: return reinterpret_cast<const void*>(mgs_cluster_kernel<kNaive, 8>);
+    case kHA: return reinterpret_cast<const void*>(mgs_cluster_kernel<kHA, 8>);
+    default:
+      return panel == 4 ? reinterpret_cast<const void*>(mgs_cluster_kernel<kHP, 4>)
+                        : reinterpret_cast<const void*>(mgs_cluster_kernel<kHP, 8>);
+  }
+}
+
+cudaError_t cluster_prepare(int device) {
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e != cudaSuccess) return e;
+  for (const auto& k : kKernelInstances) {
+    const void* fn = cluster_fn(k[0], k[1]);
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t cluster_max_size(int variant, size_t smem, int* max_size) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kMaxClusterCtas);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kMaxClusterCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int size = 0;
+  cudaError_t e = cudaOccupancyMaxPotentialClusterSize(&size, cluster_fn(variant), &cfg);
+  if (e != cudaSuccess) return e;
+  *max_size = size < kMaxClusterCtas ? size : kMaxClusterCtas;
+  return cudaSuccess;
+}
+
+cudaError_t cluster_launch(int variant, const SweepArgs& a, int ctas, size_t smem, cudaStream_t s) {
+  SweepArgs copy = a;
+  void* args[] = {&copy};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ctas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, cluster_fn(variant, a.spmm_panel), args);
 }
 
 cudaError_t sweep_max_ctas(int variant, size_t smem, int* max_ctas) {

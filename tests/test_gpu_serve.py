@@ -113,9 +113,14 @@ def test_partitioned_sms(handle):
     d = torch.device("cuda")
     Ad = tuple(torch.from_numpy(np.ascontiguousarray(x)).to(d) for x in A)
     Zd = torch.from_numpy(np.ascontiguousarray(Z.T)).to(d).T
-    Q1, R1 = handle.qr(Ad, Zd, "hp")
-    assert handle.info() == (mgsa.MGSA_OK, 0)
+    handle.set_param(mgsa.MGSA_PARAM_CLUSTER, 1)  # a whole-GPU launch, where the CTA count shows
+    try:
+        Q1, R1 = handle.qr(Ad, Zd, "hp")
+        assert handle.info() == (mgsa.MGSA_OK, 0)
+    finally:
+        handle.set_param(mgsa.MGSA_PARAM_CLUSTER, 0)
     h2 = mgsa.Handle(0)
+    h2.set_param(mgsa.MGSA_PARAM_CLUSTER, 1)
     Q2, R2 = h2.qr(Ad, Zd, "hp")
     assert h2.info() == (mgsa.MGSA_OK, 0)
     h2.close()
@@ -158,11 +163,13 @@ def test_time_sliced_large_requests(handle, variant):
         sl.close()
     assert stats["ok"] == len(reqs)
     assert stats["launches"] > stats["small"] and 0 < stats["small"] < len(reqs)
+    handle.set_param(mgsa.MGSA_PARAM_CLUSTER, 1)  # slices run on the whole GPU (its large part)
     plain = KeepingServer(handle.h, variant, **kw)
     try:
         plain.run(fresh(reqs), realtime=False)
     finally:
         plain.close()
+        handle.set_param(mgsa.MGSA_PARAM_CLUSTER, 0)
     for r in reqs:
         Q, R, info = sl.results[r.rid]
         Qp, Rp, infop = plain.results[r.rid]

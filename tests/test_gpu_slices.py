@@ -17,7 +17,9 @@ FORMS = ["naive", "ha", "hp"]
 
 @pytest.fixture(scope="module")
 def handle():
+    # Slices always run on the whole GPU; the one-call reference must too.
     h = mgsa.Handle(0)
+    h.set_param(mgsa.MGSA_PARAM_CLUSTER, 1)
     yield h
     h.close()
 

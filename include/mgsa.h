@@ -283,6 +283,16 @@ mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, 
  *                                product X = A Z (HP): 4 or 8 (0 = 8), each
  *                                width a kernel of its own; every column's
  *                                sums are the same for either width
+ *   MGSA_PARAM_WAIT_FAULT        failure-detection test hook, 0 (default) or
+ *                                1: while set, each whole-GPU MGS launch of
+ *                                this handle starts its device-wide barrier
+ *                                counter one arrival short, so its first
+ *                                device-wide wait never completes.  The wait
+ *                                is bounded (4 s): the kernel records
+ *                                MGSA_ERR_TIMEOUT, every CTA returns, and
+ *                                mgsa_get_info reports it; the context stays
+ *                                usable.  No effect on cluster, CGS, batched
+ *                                or allocation-free launches.
  * Results stay deterministic for a fixed setting; different MAX_CTAS,
  * CHUNK_ROWS, MIN_ROWS_PER_CTA, ROW_MODE or CLUSTER settings change the reduction
  * tree and therefore the last bits of Q and R (BATCH_CTAS and SPMM_PANEL do
@@ -296,7 +306,8 @@ typedef enum {
   MGSA_PARAM_BATCH_CTAS = 3,
   MGSA_PARAM_ROW_MODE = 4,
   MGSA_PARAM_SPMM_PANEL = 5,
-  MGSA_PARAM_CLUSTER = 6
+  MGSA_PARAM_CLUSTER = 6,
+  MGSA_PARAM_WAIT_FAULT = 7
 } mgsa_param;
 mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value);
 

@@ -25,6 +25,7 @@ struct mgsa_context {
   int row_mode = 0;                 // MGSA_PARAM_ROW_MODE
   int spmm_panel = 8;               // MGSA_PARAM_SPMM_PANEL
   int cluster = 0;                  // MGSA_PARAM_CLUSTER: 0 auto, 1 never, c >= 2 a cluster of c CTAs
+  bool wait_fault = false;          // MGSA_PARAM_WAIT_FAULT: first device-wide wait one arrival short
   size_t batch_smem = 0;
 };
 
@@ -287,6 +288,10 @@ mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value) {
       if (value != 0 && value != 4 && value != 8) return fail(MGSA_ERR_INVALID, "SpMM panel: 0 (default 8), 4 or 8");
       h->spmm_panel = value == 0 ? 8 : (int)value;
       return MGSA_OK;
+    case MGSA_PARAM_WAIT_FAULT:
+      if (value > 1) return fail(MGSA_ERR_INVALID, "wait fault: 0 (off) or 1 (on)");
+      h->wait_fault = value == 1;
+      return MGSA_OK;
     default: return fail(MGSA_ERR_INVALID, "unknown parameter");
   }
 }
@@ -391,6 +396,13 @@ static mgsa_status qr_launch(mgsa_handle h, const mgsa_csr* A, const double* Z, 
   cudaError_t e = step_begin == 0 ? cudaMemsetAsync(h->ctl, 0, sizeof(int) * mgsa::kCtlWords, cs)
                                   : cudaMemsetAsync(h->ctl + mgsa::kCtlBarCount, 0, 2 * sizeof(int), cs);
   if (e != cudaSuccess) return cuda_fail(e);
+  // Failure-detection test hook: with the counter at 2^32 - 1 the first
+  // barrier's arrivals wrap it to grid - 1, one short of its target grid, so
+  // every CTA's bounded wait runs out (each CTA reads the counter only after
+  // its own arrival, never the initial value).
+  if (h->wait_fault && !is_cgs(v) && !p.cluster &&
+      (e = cudaMemsetAsync(h->ctl + mgsa::kCtlBarCount, 0xFF, sizeof(int), cs)) != cudaSuccess)
+    return cuda_fail(e);
   if (is_cgs(v)) e = mgsa::cgs_launch(kernel_variant(v), a, p.grid, p.smem, cs);
   else if (p.cluster) e = mgsa::cluster_launch(kernel_variant(v), a, p.grid, p.smem, cs);
   else e = mgsa::sweep_launch(kernel_variant(v), a, p.grid, p.smem, cs);

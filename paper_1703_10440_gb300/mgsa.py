@@ -82,7 +82,7 @@ SIGNATURES = {
     "mgsa_last_error": (ctypes.c_char_p, []),
 }
 (MGSA_PARAM_MAX_CTAS, MGSA_PARAM_CHUNK_ROWS, MGSA_PARAM_MIN_ROWS_PER_CTA, MGSA_PARAM_BATCH_CTAS, MGSA_PARAM_ROW_MODE,
- MGSA_PARAM_SPMM_PANEL, MGSA_PARAM_CLUSTER) = 0, 1, 2, 3, 4, 5, 6
+ MGSA_PARAM_SPMM_PANEL, MGSA_PARAM_CLUSTER, MGSA_PARAM_WAIT_FAULT) = 0, 1, 2, 3, 4, 5, 6, 7
 
 
 def library_path() -> str:

@@ -195,6 +195,9 @@ class ClockSampler:
 # CPU oracle (baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
+CPU_SAMPLE_S = 10.0  # CPU work of the cpu_baseline sample
+
+
 def time_oracle(A, Z, variants) -> float:
     import oracle
 
@@ -360,10 +363,15 @@ def run_gpu(args, desc, A, Z, rank, world, local_rank):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        secs = time_oracle(A, Z, VARIANTS)
-        cpu = {"value": 3.0 / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one single-threaded oracle QR per variant (naive, ha, hp; plain C FP64, row form) of the "
-                         f"same {desc} input: {secs:.2f} s"}
+        # Rounds of one QR per variant until about 10 s of CPU work (one round
+        # if a single round takes longer).
+        secs, rounds = 0.0, 0
+        while rounds == 0 or secs < CPU_SAMPLE_S:
+            secs += time_oracle(A, Z, VARIANTS)
+            rounds += 1
+        cpu = {"value": 3.0 * rounds / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{rounds} round(s) of one single-threaded oracle QR per variant (naive, ha, hp; plain C "
+                         f"FP64, row form) of the same {desc} input: {3 * rounds} QRs in {secs:.2f} s"}
 
     value = world * 3 * 1e3 / step_ms_max
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

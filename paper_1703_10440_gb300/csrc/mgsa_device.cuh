@@ -158,20 +158,26 @@ __device__ __forceinline__ bool sync_all(int* ctl, unsigned int& gen, int* s_fla
 // Result of the step body: 0, or (device status << 24) | 1-based column.
 __device__ __forceinline__ int body_result(int status, int column) { return (status << 24) | (column & 0xFFFFFF); }
 
-// Sum over CTAs b (in order of b, fixed tree) of part[b * stride], by warp 0;
-// lane 0 returns the sum.
-__device__ __forceinline__ double warp0_sum_ctas(const double* part, int64_t stride, int G) {
+// Sum over CTAs b (fixed tree) of part[b * stride], by one warp: lane l adds
+// the CTAs l, l + 32, ..., l + 128 of each group of 160 in that order, then a
+// butterfly.  Every lane returns the sum.
+__device__ __forceinline__ double warp_sum_ctas(const double* part, int64_t stride, int G, int lane) {
   double t = 0.0;
   for (int b0 = 0; b0 < G; b0 += 160) {
     double v[5];
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
-      const int bb = b0 + (int)threadIdx.x + 32 * s;
+      const int bb = b0 + lane + 32 * s;
       v[s] = bb < G ? ld_cg(part + bb * stride) : 0.0;
     }
     t += (((v[0] + v[1]) + v[2]) + v[3]) + v[4];
   }
   return warp_sum(t);
+}
+
+// The same sum by warp 0 (lane = threadIdx.x).
+__device__ __forceinline__ double warp0_sum_ctas(const double* part, int64_t stride, int G) {
+  return warp_sum_ctas(part, stride, G, (int)threadIdx.x);
 }
 
 // r_ii from the norm partials: one thread forms the sum's square root, its

@@ -71,6 +71,37 @@ __device__ void reduce_first(const double* part, int G, int nt, int i, double* s
   __syncthreads();
 }
 
+// Whole-GPU launches: row i of R is summed once, spread over the CTAs, instead
+// of by every CTA.  Warp 0 sums r_{i,i+1} (needed at once by every CTA); the
+// other warps of CTA b sum r_{i,j} for j = i + 2 + b + G t and store them in R.
+// Each CTA reloads the row from R after the next step's first device-wide
+// wait, which orders these stores before the loads.
+__device__ void reduce_first_dist(const double* part, int G, int nt, int i, double* s_rrow, double* R, int ldr,
+                                  int kg, int b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    const double r = warp_sum_ctas(part + (i + 1), nt, G, lane);
+    if (lane == 0) {
+      s_rrow[i + 1] = r;
+      if (b == 0) R[i + (int64_t)(i + 1 - kg) * ldr] = r;
+    }
+  } else {
+    for (int64_t j = i + 2 + b + (int64_t)G * (warp - 1); j < nt; j += (int64_t)G * (kWarps - 1)) {
+      const double r = warp_sum_ctas(part + j, nt, G, lane);
+      if (lane == 0) R[i + (j - kg) * ldr] = r;
+    }
+  }
+  __syncthreads();
+}
+
+// Row i-1 of R, columns j > i (summed by reduce_first_dist at the end of step
+// i-1), into s_rrow; warps 1.. load it while warp 0 forms the diagonal.
+__device__ __forceinline__ void reload_row(const double* R, int ldr, int kg, int i, int nt, double* s_rrow) {
+  if (threadIdx.x >= 32)
+    for (int j = i + 1 + (int)threadIdx.x - 32; j < nt; j += kThreads - 32)
+      s_rrow[j] = ld_cg(R + (i - 1) + (int64_t)(j - kg) * ldr);
+}
+
 constexpr int kTripRows = 8;                     // rows per lane per trip of the fused pass
 
 // The fused pass over one chunk of rows [c0, c0 + crows) and the columns
@@ -155,6 +186,9 @@ __device__ __forceinline__ void fused_pass(int i, int jbeg, int ncols, int kg, i
 template <int V, bool kBatch, int kPanel, bool kSliced, bool kCluster = false>
 __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* smem, int* s_wfirst, int* s_wlast,
                           int* s_flags) {
+  // Row sums of R spread over the CTAs (whole-GPU launches), or summed by
+  // every CTA (one CTA or one cluster per instance).
+  constexpr bool kDist = !kBatch && !kCluster;
   const int n = a.n;    // columns of Z
   const int kg = a.kg;  // given columns before them (successive orthogonalisation)
   const int nt = kg + n;
@@ -314,7 +348,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       }
       MGSA_TRACE(i, 1);
       sync_arrive<kBatch, kCluster>(a.ctl, gen, s_flags);
-      if (rest_prev)  // r_{i-1,j}, j > i
+      if (!kDist && rest_prev)  // r_{i-1,j}, j > i
         reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
       if (!sync_wait<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     } else {
@@ -355,7 +389,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         }
         MGSA_TRACE(i, 10);
         sync_arrive<kBatch, kCluster>(a.ctl, gen, s_flags);
-        if (rest_prev)
+        if (!kDist && rest_prev)
           reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
         MGSA_TRACE(i, 11);
         if (!sync_wait<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
@@ -435,6 +469,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       if (!sync_all<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     }
     MGSA_TRACE(i, 2);
+    if (kDist && rest_prev) reload_row(R, ldr, kg, i, nt, s_rrow);  // r_{i-1,j}, j > i
     diagonal(part_norm, G, s_scal);
     MGSA_TRACE(i, 3);
     if (s_scal[2] != 0.0) return body_result((int)s_scal[2], i + 1 - kg);  // the same verdict in every CTA
@@ -588,12 +623,12 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     MGSA_TRACE(i, 8);
     if (given) {
       reduce_range(part_cur, G, nt, jbeg, nt, s_rrow, s_buf, b == 0 ? R + i : nullptr, ldr, kg);  // all of row i
+    } else if (kDist) {
+      // r_{i,i+1} here, r_{i,j} (j > i + 1) spread over the CTAs into R; a
+      // later slice reloads the row from R as the next step would.
+      reduce_first_dist(part_cur, G, nt, i, s_rrow, R, ldr, kg, b);
     } else {
       reduce_first(part_cur, G, nt, i, s_rrow, R, ldr, kg, b == 0);  // r_{i,i+1}; the rest at the next wait
-      // The last step of a slice sums the rest of row i now, with the same
-      // trees as the next step's wait would, for the next slice to reload.
-      if (kSliced && i + 1 == i1)
-        reduce_range(part_cur, G, nt, i + 2, nt, s_rrow, s_buf, b == 0 ? R + i : nullptr, ldr, kg);
     }
     MGSA_TRACE(i, 9);
   }

@@ -17,7 +17,12 @@ the total over the QR.  The traced kernel records at these points:
               6   warp pieces of the row partials combined
               7   CTA partials stored
               8   row barrier passed
-              9   r_{i,i+1} summed
+              9   r_{i,i+1} summed (whole-GPU launches: and this CTA's share
+                  of the rest of row i)
+
+When a CTA's rows exceed one pivot chunk (staged mode), slots 4 and 5 are
+recorded once per chunk and the last chunk's times remain: "pivots" then
+also holds the fused passes of the earlier chunks.
 
 Usage: python -m paper_1703_10440_gb300.phase_trace [poisson2d|varcoef3d|tridiag|denseband]
 Needs a GPU.  Diagnostic only: the product build has no trace code.

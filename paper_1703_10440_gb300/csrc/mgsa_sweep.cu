@@ -20,9 +20,11 @@
 // over the remaining columns.  Division by r_ii is a multiplication by the
 // reciprocal, formed once per step.
 //
-// Only r_{i,i+1} is needed before the next step's first barrier; the other
-// r_ij are summed while that barrier is pending (split arrive / wait), with
-// the per-CTA partials double-buffered by step parity.
+// Only r_{i,i+1} is needed before the next step's first barrier.  In a
+// whole-GPU launch the other r_ij are summed once, spread over the CTAs, into
+// R, and every CTA reloads them after that barrier; in a one-CTA (batched) or
+// one-cluster launch every CTA sums them while that barrier is pending (split
+// arrive / wait).  The per-CTA partials are double-buffered by step parity.
 //
 // On GB300 one warp-wide FP64 instruction holds the FP64 pipe for ~16 cycles,
 // so every FP64 operation outside the fused pass is done once (not once per

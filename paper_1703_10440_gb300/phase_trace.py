@@ -8,8 +8,9 @@ the total over the QR.  The traced kernel records at these points:
     step slot 0   step start
               1   norm partial of column i stored (HP: after the L update;
                   HA / naive: after the z_i update, its barrier and the MV)
-              2   norm barrier passed (HP: the window holds the reduction of
-                  the rest of row i-1)
+              2   norm barrier passed (one-cluster launches: the window
+                  holds the reduction of the rest of row i-1; whole-GPU
+                  launches reload that row from R after it)
               3   r_ii formed (diagonal)
               4   pivots q_i, p_i formed (naive: after the second MV and its
                   barrier)

@@ -235,3 +235,38 @@ def test_parity_long_rows_multi_chunk(handle, variant):
         handle.set_param(mgsa.MGSA_PARAM_CHUNK_ROWS, 0)
     assert (st, info) == (mgsa.MGSA_OK, 0)
     check_parity(A, Z, variant, Q, R)
+
+
+@pytest.mark.parametrize("variant", VARIANTS + ["cgs_naive", "cgs_ha", "cgs_hp"])
+@pytest.mark.parametrize("min_rows,chunk", [(0, 0), (32, 0), (0, 64)])
+def test_max_width_closed_form(handle, variant, min_rows, chunk):
+    """The widest QR the library takes, n = MGSA_MAX_N = 2048 with m = n.  Z
+    is the whole sine eigenbasis U of tridiag(-1, 2.1, -1) with columns scaled
+    by s_k, so Z^T A Z = diag(s_k^2 lambda_k): R = diag(s_k sqrt(lambda_k))
+    and Q = U diag(1 / sqrt(lambda_k)) exactly (the closed form the oracle is
+    pinned to at small sizes; the oracle's own HP run at this size is within
+    1e-13 (R) and 2.5e-13 (Q) of it, relative to the largest entry, and so is
+    its CGS-HA run).  MGS and CGS forms; 16 CTAs (default), 64 CTAs (every
+    CTA then sums about 32 entries of each row of R), and pivots staged in
+    64-row chunks."""
+    m = n = mgsa.MGSA_MAX_N
+    A = W.tridiag_csr(m)
+    t = np.arange(1, m + 1)
+    ks = np.arange(1, n + 1)
+    U = np.sqrt(2.0 / (m + 1)) * np.sin(np.outer(t, ks) * np.pi / (m + 1))
+    lam = 2.1 - 2.0 * np.cos(ks * np.pi / (m + 1))
+    scale = 1.0 + (ks % 7) / 4.0
+    Z = U * scale[None, :]
+    handle.set_param(mgsa.MGSA_PARAM_MIN_ROWS_PER_CTA, min_rows)
+    handle.set_param(mgsa.MGSA_PARAM_CHUNK_ROWS, chunk)
+    try:
+        Q, R, st, info = gpu_qr(handle, A, Z, variant)
+    finally:
+        handle.set_param(mgsa.MGSA_PARAM_MIN_ROWS_PER_CTA, 0)
+        handle.set_param(mgsa.MGSA_PARAM_CHUNK_ROWS, 0)
+    assert (st, info) == (mgsa.MGSA_OK, 0)
+    Rexp = np.diag(np.sqrt(lam) * scale)
+    Qexp = U / np.sqrt(lam)[None, :]
+    assert np.all(np.tril(R, -1) == 0.0) and np.all(np.diag(R) > 0)
+    assert np.abs(R - Rexp).max() <= 1e-11 * np.abs(Rexp).max()
+    assert np.abs(Q - Qexp).max() <= 1e-11 * np.abs(Qexp).max()

@@ -394,7 +394,7 @@ def run_batch(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    inst = W.batch(4096)
+    inst = W.batch(args.batch_count)
     # largest work first for the queue's load balance
     order = sorted(range(len(inst)), key=lambda k: -inst[k][1].shape[0] * inst[k][1].shape[1] ** 2)
     inst = [inst[k] for k in order]
@@ -469,7 +469,7 @@ def run_batch(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": world * 3 * len(inst) * 1e3 / step_ms_max, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batch4096_banded_hb8_m256-8192_n4-64", "instances": len(inst),
+            "config": {"workload": f"batch{len(inst)}_banded_hb8_m256-8192_n4-64", "instances": len(inst),
                        "step": "one mgsa_qr_batched call per variant (naive, ha, hp)",
                        "l2": "flushed (256 MiB write) before every timed call"},
             "per_variant": per_variant,
@@ -569,6 +569,8 @@ def main():
     ap.add_argument("--impl", default="mgsa", choices=["mgsa", "reference"])
     ap.add_argument("--workload", default="poisson2d",
                     choices=["poisson2d", "varcoef3d", "tridiag", "denseband", "batch4096", "served"])
+    ap.add_argument("--batch-count", type=int, default=4096,
+                    help="batch4096: instances per batched call (4096 is the workload; fewer for profiling)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="served: arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="served: arrival window")
     ap.add_argument("--serve-variant", default="hp", choices=["naive", "ha", "hp"])

@@ -17,10 +17,12 @@
 //   F   q_j = z_j / r_jj, p_j = x_j / r_jj (eq. (tec1)); p_j^T z_{j+1}^{(0)}.
 //
 // Device-wide waits per column: HP two (the norm after U; r_{j,j+1} after F),
-// HA and naive three (the MV gathers z_j from other CTAs' rows).  Only
-// r_{j,j+1} is summed on the critical path; r_{i,j+1} (i < j) are summed while
-// a barrier is pending.  CTA b owns rows [b*rpc, (b+1)*rpc) of every column;
-// only the MV gathers and the partial sums cross CTAs.
+// HA and naive three (the MV gathers z_j from other CTAs' rows).  Every CTA
+// sums r_{j,j+1} after the last wait of column j; r_{i,j+1} (i < j) are summed
+// once, spread over the CTAs (CTA b takes i = b + G t), off the critical path,
+// stored in R and reloaded by every CTA after that wait.  CTA b owns rows
+// [b*rpc, (b+1)*rpc) of every column; only the MV gathers and the partial
+// sums cross CTAs.
 //
 // U streams every earlier pivot once per column.  F stores q_j, p_j of the
 // CTA's rows as one contiguous block per (pivot, CTA), and U fetches each
@@ -360,6 +362,19 @@ __device__ double mv_rows(const int32_t* __restrict__ rowptr, const int32_t* __r
   return sl;
 }
 
+// r_{i,j+1}, i < j, summed once over the CTAs: warps 1.. of CTA b sum the
+// entries i = b + G t (the partials of every CTA are complete) and store them
+// in column j+1 of R; every CTA reloads that column after the column's last
+// device-wide wait.  Warp 0 is left free for the diagonal.
+__device__ __forceinline__ void sum_assigned(const double* part, int G, int n, int j, double* R, int ldr, int b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) return;
+  for (int64_t i = b + (int64_t)G * (warp - 1); i < j; i += (int64_t)G * (kWarps - 1)) {
+    const double r = warp_sum_ctas(part + i, n, G, lane);
+    if (lane == 0) R[i + (int64_t)(j + 1) * ldr] = r;
+  }
+}
+
 template <int V, int kPanel>
 __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* smem, uint64_t* s_full,
                         uint64_t* s_empty, int* s_flags) {
@@ -498,11 +513,13 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
       CGS_TRACE(j, 3);
       sync_arrive<false>(a.ctl, gen, s_flags);
       // r_{i,j+1}, i < j: their partials were stored before the previous wait.
-      if (has_next && j > 0)
-        reduce_range(part_cur, G, n, 0, j, s_rnext, s_buf, b == 0 ? R + (int64_t)(j + 1) * ldr : nullptr, 1, 0);
+      if (has_next && j > 0) sum_assigned(part_cur, G, n, j, R, ldr, b);
       if (!sync_wait<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     }
     CGS_TRACE(j, 4);
+    // HP: r_{i,j+1}, i < j (partials stored before the norm wait), while warp 0
+    // forms r_jj.
+    if (V == kHP && has_next && j > 0) sum_assigned(part_cur, G, n, j, R, ldr, b);
     diagonal(part_norm, G, s_scal);
     CGS_TRACE(j, 5);
     if (s_scal[2] != 0.0) return body_result((int)s_scal[2], j + 1);  // the same verdict in every CTA
@@ -554,10 +571,7 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
     CGS_TRACE(j, 7);
 
     // ---------------- r_{:,j+1} ----------------
-    sync_arrive<false>(a.ctl, gen, s_flags);
-    if (V == kHP && j > 0)
-      reduce_range(part_cur, G, n, 0, j, s_rnext, s_buf, b == 0 ? R + (int64_t)(j + 1) * ldr : nullptr, 1, 0);
-    if (!sync_wait<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+    if (!sync_all<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
     CGS_TRACE(j, 8);
     if (tid < 32) {
       const double r = warp0_sum_ctas(part_cur + j, n, G);
@@ -565,6 +579,9 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
         s_rnext[j] = r;
         if (b == 0) R[j + (int64_t)(j + 1) * ldr] = r;
       }
+    } else {
+      // r_{i,j+1}, i < j, summed by their CTAs into R before this wait
+      for (int i = tid - 32; i < j; i += kThreads - 32) s_rnext[i] = ld_cg(R + i + (int64_t)(j + 1) * ldr);
     }
     __syncthreads();
     CGS_TRACE(j, 9);

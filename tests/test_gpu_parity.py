@@ -270,3 +270,55 @@ def test_max_width_closed_form(handle, variant, min_rows, chunk):
     assert np.all(np.tril(R, -1) == 0.0) and np.all(np.diag(R) > 0)
     assert np.abs(R - Rexp).max() <= 1e-11 * np.abs(Rexp).max()
     assert np.abs(Q - Qexp).max() <= 1e-11 * np.abs(Qexp).max()
+
+
+ALL_FORMS = VARIANTS + ["cgs_naive", "cgs_ha", "cgs_hp"]
+
+
+def oracle_form(A, Z, form):
+    if form.startswith("cgs_"):
+        return oracle.cgs(A, Z, form[4:], "col")
+    return oracle.mgs(A, Z, form, "row")
+
+
+@pytest.mark.parametrize("form", ALL_FORMS)
+def test_identity_matches_householder(handle, form):
+    """A = I: the A-inner product is the Euclidean one, so every form computes
+    the Householder QR of Z with the signs fixed so that diag(R) > 0 (numpy's
+    LAPACK QR, not the oracle)."""
+    m, n = 3001, 40
+    A = (np.arange(m + 1, dtype=np.int32), np.arange(m, dtype=np.int32), np.ones(m))
+    Z = W.rng(6, 301).standard_normal((m, n))
+    Q, R, st, info = gpu_qr(handle, A, Z, form)
+    assert (st, info) == (mgsa.MGSA_OK, 0)
+    Qh, Rh = np.linalg.qr(Z)
+    s = np.sign(np.diag(Rh))
+    Qh, Rh = Qh * s[None, :], Rh * s[:, None]
+    assert np.abs(R - Rh).max() <= 1e-12 * np.abs(Rh).max()
+    assert np.abs(Q - Qh).max() <= 1e-12 * np.abs(Qh).max()
+
+
+@pytest.mark.parametrize("form", ALL_FORMS)
+def test_empty_rows_and_empty_matrix(handle, form):
+    """CSR rows without entries.  A = diag(d) with every other row empty is
+    positive definite on the even rows, where Z lives: the QR succeeds and
+    matches the oracle's.  A with no entries at all (nnz = 0, no column or
+    value array) breaks down at column 1."""
+    m, n = 2003, 9
+    d = np.where(np.arange(m) % 2 == 0, 1.0 + np.arange(m) / m, 0.0)
+    rows = np.nonzero(d)[0]
+    rowptr = np.zeros(m + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum(d != 0)
+    A = (rowptr, rows.astype(np.int32), d[rows])
+    Z = W.rng(6, 302).standard_normal((m, n))
+    Z[1::2, :] = 0.0
+    Q, R, st, info = gpu_qr(handle, A, Z, form)
+    assert (st, info) == (mgsa.MGSA_OK, 0)
+    Qo, Ro, oinfo, _, _ = oracle_form(A, Z, form)
+    assert oinfo == 0
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 1e-10
+    assert np.abs(Q - Qo).max() <= 1e-10 * np.abs(Qo).max()
+    assert np.all(Q[1::2, :] == 0.0)
+    A0 = (np.zeros(m + 1, dtype=np.int32), np.zeros(0, dtype=np.int32), np.zeros(0))
+    _, _, st, info = gpu_qr(handle, A0, Z, form)
+    assert (st, info) == (mgsa.MGSA_ERR_BREAKDOWN, 1)

@@ -478,34 +478,45 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     inv = s_scal[1];
     if (b == 0 && tid == 0) R[i + (int64_t)(i - kg) * ldr] = s_scal[0];
 
-    if (V == kNaive) {
-      // p_i = A q_i with q_i = z_i / r_ii formed on the fly (Algorithm 4's second MV).
-      const double* zsrc = (i > 0) ? zi : Z;
+    if (V == kNaive && resident) {
+      // q_i = z_i / r_ii on this CTA's rows, into Q (no CTA reads z_i after
+      // the norm wait); after the next wait the second MV of Algorithm 4,
+      // p_i = A q_i, gathers it, with no multiply per nonzero.
+#pragma unroll
+      for (int t = 0; t < kResRows; ++t) {
+        const int rr = tid + t * kThreads;
+        if (rr < crows_all) zi[k0 + rr] = zr[t] * inv;
+      }
+      if (!sync_all<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
       if (a.mv_warp) {
         const int lane = tid & 31, warp = tid >> 5;
         double* ptmp = s_piv + (2 * cur + 1) * chunk;
         for (int64_t k = k0 + warp; k < k1; k += kWarps) {
-          const double pk = csr_row_warp(rowptr, colidx, val, zsrc, inv, true, k);
-          if (lane == 0) {
-            if (resident) ptmp[k - k0] = pk;
-            else X[k + ldx] = pk;
-          }
+          const double pk = csr_row_warp(rowptr, colidx, val, zi, 1.0, false, k);
+          if (lane == 0) ptmp[k - k0] = pk;
         }
-        if (resident) {
-          __syncthreads();
+        __syncthreads();
 #pragma unroll
-          for (int t = 0; t < kResRows; ++t) {
-            const int rr = tid + t * kThreads;
-            xr[t] = rr < crows_all ? ptmp[rr] : 0.0;
-          }
+        for (int t = 0; t < kResRows; ++t) {
+          const int rr = tid + t * kThreads;
+          xr[t] = rr < crows_all ? ptmp[rr] : 0.0;
         }
-      } else if (resident) {
+      } else {
 #pragma unroll
         for (int h = 0; h < kResRows / 4; ++h) {
           double pv[4];
-          csr_rows4(rowptr, colidx, val, zsrc, inv, true, k0 + tid + (int64_t)h * 4 * kThreads, k1, pv);
+          csr_rows4(rowptr, colidx, val, zi, 1.0, false, k0 + tid + (int64_t)h * 4 * kThreads, k1, pv);
 #pragma unroll
           for (int q = 0; q < 4; ++q) xr[4 * h + q] = pv[q];
+        }
+      }
+    } else if (V == kNaive) {
+      // p_i = A q_i with q_i = z_i / r_ii formed on the fly (Algorithm 4's second MV).
+      const double* zsrc = (i > 0) ? zi : Z;
+      if (a.mv_warp) {
+        for (int64_t k = k0 + (tid >> 5); k < k1; k += kWarps) {
+          const double pk = csr_row_warp(rowptr, colidx, val, zsrc, inv, true, k);
+          if ((tid & 31) == 0) X[k + ldx] = pk;
         }
       } else {
         for (int64_t k = k0 + tid; k < k1; k += 4 * kThreads) {
@@ -544,7 +555,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
               pv = a.Pg[k0 + rr + (int64_t)i * a.ldpg];
             } else {
               qv = zr[t] * inv;
-              zi[k0 + rr] = qv;
+              if (V != kNaive) zi[k0 + rr] = qv;  // naive: stored before its second MV
               pv = (V == kNaive) ? xr[t] : xr[t] * inv;
               if (V == kHP) xcol(i)[k0 + rr] = pv;
               else if (a.Pout) a.Pout[k0 + rr + (int64_t)(i - kg) * a.ldpo] = pv;

@@ -119,7 +119,9 @@ size_t mgsa_workspace_bytes(mgsa_handle h, int64_t m, int n, mgsa_variant v);
  *          overlapping Z at all.
  *          Q is also the working storage of the z_j^{(i)} columns.
  *   R      n x n output, leading dimension ldr >= n; written in full, zeros
- *          below the diagonal.
+ *          below the diagonal.  The CTAs of one launch also pass the sums of
+ *          each row (column for CGS) to each other through R; its contents
+ *          are final once the queued work has completed.
  *   s      stream the work is queued on; the call returns without waiting.
  *
  * Requirements: 1 <= n <= MGSA_MAX_N, n <= m < 2^31, nnz < 2^31.

@@ -231,6 +231,46 @@ def run_reference(args, desc, A, Z, rank):
     print(json.dumps(line), flush=True)
 
 
+REF_BATCH_SAMPLE = 64  # instances per step of the batched workload's oracle arm
+
+
+def run_reference_batch(args, rank):
+    """Oracle arm of the batched workload: each step runs the single-threaded
+    oracle on a fixed sample of the batch's instances (one QR each, the forms
+    taking turns by step); QR/s over the sample."""
+    if rank != 0:
+        return
+    inst = W.batch(args.batch_count)
+    sample = inst[:: max(1, len(inst) // REF_BATCH_SAMPLE)][:REF_BATCH_SAMPLE]
+    for k in range(args.warmup):
+        time_oracle_many(sample, VARIANTS[k % 3])
+    secs = [time_oracle_many(sample, VARIANTS[k % 3]) for k in range(args.steps)]
+    total = sum(secs)
+    value = len(sample) * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batch{len(inst)}_banded_hb8_m256-8192_n4-64", "instances": len(inst),
+                       "step": f"one QR of each of {len(sample)} sampled instances, the forms taking turns by step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"every {max(1, len(inst) // REF_BATCH_SAMPLE)}-th instance of the batch "
+                                       f"({len(sample)} of {len(inst)}), single-threaded plain C FP64 oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_oracle_many(instances, variant) -> float:
+    import oracle
+
+    oracle.load()
+    t0 = time.perf_counter()
+    for A, Z in instances:
+        _, _, info, _, _ = oracle.mgs(A, Z, variant, "row")
+        if info != 0:
+            raise RuntimeError(f"oracle breakdown in {variant}")
+    return time.perf_counter() - t0
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -592,7 +632,15 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        if rank == 0:
+        if rank != 0:
+            return
+        if args.workload == "batch4096":
+            run_reference_batch(args, rank)
+        elif args.workload == "served":
+            print(json.dumps({"impl": "reference", "unavailable": "the served stream's inputs are drawn on the GPU at "
+                                                                  "admission; the oracle arm covers the single-instance "
+                                                                  "and batched workloads"}), flush=True)
+        else:
             desc, A, Z = make_workload(args.workload)
             run_reference(args, desc, A, Z, rank)
         return

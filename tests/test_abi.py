@@ -76,3 +76,29 @@ def test_plain_c_client_builds_and_fails_cleanly_without_gpu(tmp_path):
         return  # the GPU run is tests/test_gpu_c_client.py
     r = subprocess.run([exe, "100", "4", "1"], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.startswith("nogpu"), (r.stdout, r.stderr)
+
+
+def header_constants():
+    """Enumerators (NAME = integer) and integer #defines of include/*.h."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for name, val in re.findall(r"\b(MGSA_\w+)\s*=\s*(-?\d+)\s*[,}]", text):
+            out[name] = int(val)
+        for name, val in re.findall(r"^#define\s+(MGSA_\w+)\s+\(?(-?\d+)\)?\s*$", text, flags=re.M):
+            out[name] = int(val)
+        for name, val, sh in re.findall(r"^#define\s+(MGSA_\w+)\s+\((\d+)u\s*<<\s*(\d+)\)", text, flags=re.M):
+            out[name] = int(val) << int(sh)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    consts = header_constants()
+    for name in ("MGSA_NAIVE", "MGSA_CGS_HP", "MGSA_ERR_TIMEOUT", "MGSA_PARAM_WAIT_FAULT", "MGSA_MAX_N",
+                 "MGSA_BATCH_MAX_N", "MGSA_NOALLOC_SCRATCH_BYTES"):
+        assert name in consts, name
+    for name, val in consts.items():
+        if hasattr(mgsa, name):
+            assert getattr(mgsa, name) == val, (name, getattr(mgsa, name), val)
+    missing = sorted(n for n in consts if not hasattr(mgsa, n))
+    assert not missing, missing

@@ -335,7 +335,10 @@ mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value);
  * Runs on the current CUDA device; every pointer must be on that device.
  * The first call on a device sets that device up (looks up the address of
  * the static array and sets the kernel's shared-memory limit); make that
- * first call before any stream capture.  Problems whose scratch does not fit
+ * first call before any stream capture.  That set-up belongs to the CUDA
+ * context: each call checks the id of the current context, and the first
+ * call in a new context on the device -- after cudaDeviceReset, for example --
+ * repeats it, so it too should come before any stream capture.  Problems whose scratch does not fit
  * (about 8*(m*c + (2n+1)*G) bytes with c = n for HP, 1 for HA, 2 for naive and
  * G <= the number of SMs) are rejected with MGSA_ERR_INVALID and a message
  * in mgsa_last_error; nothing is launched then.  Every call uses the same
@@ -346,6 +349,21 @@ mgsa_status mgsa_set_param(mgsa_handle h, mgsa_param p, int64_t value);
 #define MGSA_NOALLOC_SCRATCH_BYTES (32u << 20)
 mgsa_status mgsa_qr_noalloc(const mgsa_csr* A, const double* Z, int64_t m, int n, int64_t ldz, mgsa_variant v,
                             double* Q, int64_t ldq, double* R, int ldr, int* info_dev, mgsa_stream_t s);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement.                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* The FP64 fused multiply-add rate of device `device`, measured: a kernel in
+ * which every thread runs 8 independent FMA chains for `iters` iterations on
+ * 4 CTAs of 256 threads per SM, timed (after one untimed launch) with CUDA
+ * events on a stream of its own.  *tflops = 2 * FMAs / time in TFLOP/s, *ms the
+ * timed launch's duration.  The paper has no counterpart: this is the
+ * ceiling against which the FP64-bound sweep kernels are measured.  It
+ * allocates a small output buffer, synchronises the device's new stream and
+ * restores the current device.  MGSA_ERR_INVALID for NULL outputs, iters < 1
+ * or a bad device; MGSA_ERR_CUDA if a CUDA call fails. */
+mgsa_status mgsa_fp64_probe(int device, int iters, double* tflops, double* ms);
 
 /* Short static description of the most recent failure on this thread
  * (never NULL). */

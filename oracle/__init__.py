@@ -12,6 +12,9 @@ Everything here is a thin ctypes wrapper around ``mgs_oracle.c``:
 * :func:`cgs` runs the classical Gram-Schmidt counterparts (CGS-naive / HA /
   HP, both forms), :func:`mgs_append` continues the column form after k given
   A-orthonormal columns.
+* :func:`mgs_par` runs the row-oriented Algorithms 4 / 7 / 8 on several host
+  cores (``mgs_oracle_par.c``); it performs the same operations in the same
+  order as :func:`mgs` and returns the same bits.
 * :func:`repr_error`, :func:`orth_loss` and :func:`chol_gram` evaluate the
   representation error ``||Z - QR||_F / ||Z||_F``, the loss of A-orthogonality
   ``||I - Q^T A Q||_F`` (both in double-double) and the long-double Cholesky
@@ -65,6 +68,56 @@ def _bind(lib):
     lib.oracle_chol_gram_ld.restype = ctypes.c_int
     lib.oracle_chol_gram_ld.argtypes = [i64, i32, ip, ip, dp, dp, i64, dp, i32]
     return lib
+
+
+_par_lib = None
+
+
+def load_par():
+    """Load (building if needed) the multi-core build of the row-oriented
+    algorithms (``mgs_oracle_par.c``)."""
+    global _par_lib
+    if _par_lib is None:
+        lib = ctypes.CDLL(_build.build_par())
+        i64, i32, p = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        lib.oracle_par_mgs_row.restype = ctypes.c_int
+        lib.oracle_par_mgs_row.argtypes = [i32, i64, i32, p, p, p, p, i64, p, i64, p, i32, ctypes.POINTER(ctypes.c_int)]
+        lib.oracle_par_threads.restype = ctypes.c_int
+        lib.oracle_par_threads.argtypes = []
+        lib.oracle_par_set_threads.restype = None
+        lib.oracle_par_set_threads.argtypes = [i32]
+        _par_lib = lib
+    return _par_lib
+
+
+def par_threads(threads: int | None = None) -> int:
+    """Set (if given) and return the thread count of :func:`mgs_par`."""
+    lib = load_par()
+    if threads:
+        lib.oracle_par_set_threads(int(threads))
+    return int(lib.oracle_par_threads())
+
+
+def mgs_par(A, Z: np.ndarray, variant: str = "naive", threads: int | None = None):
+    """Algorithm 4 / 7 / 8 (row form) on several host cores: the same
+    operations as ``mgs(A, Z, variant, "row")`` in the same order, so the same
+    bits, with independent rows and columns spread over OpenMP threads.
+    Returns ``(Q, R, info, kind)``.  Parity: pinned bitwise to :func:`mgs` by
+    ``tests/test_oracle_par.py``."""
+    lib = load_par()
+    if threads:
+        lib.oracle_par_set_threads(int(threads))
+    rowptr, col, val = _csr_arrays(A)
+    Zf = _fortran(Z)
+    m, n = Zf.shape
+    Q = np.empty((m, n), dtype=np.float64, order="F")
+    R = np.empty((n, n), dtype=np.float64, order="F")
+    kind = ctypes.c_int(0)
+    info = lib.oracle_par_mgs_row(VARIANTS[variant], m, n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(Zf), m, _ptr(Q),
+                                  m, _ptr(R), n, ctypes.byref(kind))
+    if info < 0:
+        raise ValueError("oracle_par_mgs_row: invalid arguments")
+    return Q, R, int(info), int(kind.value)
 
 
 def _ptr(a: np.ndarray):

@@ -10,8 +10,16 @@
 // source of its scratch differs.  The array below is module data: every GPU
 // that loads the library holds it until the process exits.  Host code may not
 // use its name as a device address (on the host it names a stand-in), so the
-// first call on each device, with that device current, looks the address up
-// with cudaGetSymbolAddress and remembers it.
+// first call in each CUDA context, with that context current, looks the
+// address up with cudaGetSymbolAddress and sets the kernel's shared-memory
+// limit.  Both belong to the context: after cudaDeviceReset (or whenever
+// another context becomes current on the device) the module is loaded again,
+// possibly elsewhere, and the attribute is gone.  So the set-up is keyed on
+// the current context's unique id (cuCtxGetId, reached through the runtime's
+// driver entry points; no link to the driver library), and redone when it
+// changes.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -29,7 +37,16 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+struct DeviceSetup {
+  unsigned long long ctx_id = 0;  // id of the context the set-up was done in (0: none yet)
+  void* addr = nullptr;           // device address of g_noalloc_scratch in that context
+};
+DeviceSetup g_setup[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
 
 int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
 
@@ -43,19 +60,55 @@ mgsa_status cuda_fail(cudaError_t e) {
   return MGSA_ERR_CUDA;
 }
 
-// Once per device, with that device current: the array's device address and
-// the kernel's shared-memory attribute.
+// The unique id of the context current on this thread; when none is current
+// yet, the device's primary context is initialised and made current first.
+// Caller holds g_setup_mutex.
+mgsa_status current_context_id(int dev, unsigned long long* id) {
+  cudaError_t e = cudaSuccess;
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+    if ((e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1)) != cudaSuccess)
+      return cuda_fail(e);
+    if ((e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2)) != cudaSuccess)
+      return cuda_fail(e);
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return fail(MGSA_ERR_CUDA, "the driver does not provide cuCtxGetCurrent / cuCtxGetId");
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return fail(MGSA_ERR_CUDA, "cuCtxGetCurrent failed");
+  if (!ctx) {
+    if ((e = cudaSetDevice(dev)) != cudaSuccess) return cuda_fail(e);
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return fail(MGSA_ERR_CUDA, "no current CUDA context");
+  }
+  if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return fail(MGSA_ERR_CUDA, "cuCtxGetId failed");
+  return MGSA_OK;
+}
+
+// Once per context, with that context current: the array's device address and
+// the kernel's shared-memory attribute.  Later calls in the same context reuse
+// them; a call in a new context (after cudaDeviceReset, say) repeats both.
 mgsa_status device_setup(int dev, unsigned char** scratch) {
   if (dev < 0 || dev >= kMaxDevices) return fail(MGSA_ERR_INVALID, "device ordinal beyond the set-up table");
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  unsigned long long id = 0;
+  mgsa_status st = current_context_id(dev, &id);
+  if (st != MGSA_OK) return st;
+  DeviceSetup& d = g_setup[dev];
+  if (d.ctx_id != id || !d.addr) {
+    d.ctx_id = 0;
+    d.addr = nullptr;
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e);
     if ((e = mgsa::sweep_prepare(dev)) != cudaSuccess) return cuda_fail(e);
-    g_scratch_addr[dev] = p;
+    d.addr = p;
+    d.ctx_id = id;
   }
-  *scratch = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  *scratch = static_cast<unsigned char*>(d.addr);
   return MGSA_OK;
 }
 

@@ -79,6 +79,7 @@ SIGNATURES = {
     "mgsa_qr_batched": (_INT, [_VP, _INT, _VP, _VP, _VP]),
     "mgsa_qr_append": (_INT, [_VP, ctypes.POINTER(mgsa_csr), _VP, _I64, _VP, _I64, _INT, _VP, _I64, _INT, _I64, _INT,
                               _VP, _I64, _VP, _I64, _VP, _INT, _VP]),
+    "mgsa_fp64_probe": (_INT, [_INT, _INT, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mgsa_last_error": (ctypes.c_char_p, []),
 }
 (MGSA_PARAM_MAX_CTAS, MGSA_PARAM_CHUNK_ROWS, MGSA_PARAM_MIN_ROWS_PER_CTA, MGSA_PARAM_BATCH_CTAS, MGSA_PARAM_ROW_MODE,
@@ -131,6 +132,13 @@ def _check(status: int):
 
 def mgsa_last_error() -> str:
     return lib().mgsa_last_error().decode()
+
+
+def mgsa_fp64_probe(device: int = 0, iters: int = 20000) -> tuple[float, float]:
+    """Measured FP64 FMA rate of the device: ``(TFLOP/s, ms of the timed launch)``."""
+    tf, ms = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().mgsa_fp64_probe(device, iters, ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def mgsa_create(device: int = 0) -> int:

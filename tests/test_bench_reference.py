@@ -25,7 +25,7 @@ def check_line(d):
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["value"] > 0 and d["unit"] == "QR/s" and d["higher_is_better"] is True
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
 
@@ -34,6 +34,48 @@ def test_reference_single_instance():
     d = run("--workload", "tridiag")
     check_line(d)
     assert d["config"]["workload"] == "tridiag_m4096_n16"
+    assert d["cpu_baseline"]["cores"] == bench_module().host_cores() or d["cpu_baseline"]["cores"] == 1
+
+
+def bench_module():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    return bench
+
+
+def test_default_workload_is_the_3d_laplacian():
+    import argparse
+
+    b = bench_module()
+    seen = {}
+
+    def fake_parse(self, *a, **k):
+        seen.update({act.dest: act.default for act in self._actions})
+        raise SystemExit(0)
+
+    orig = argparse.ArgumentParser.parse_args
+    argparse.ArgumentParser.parse_args = fake_parse
+    try:
+        try:
+            b.main()
+        except SystemExit:
+            pass
+    finally:
+        argparse.ArgumentParser.parse_args = orig
+    assert seen["workload"] == "varcoef3d" and seen["gpus"] == 1 and seen["warmup"] >= 3
+
+
+def test_cpu_baseline_all_cores_and_single_thread():
+    import workloads as W
+
+    b = bench_module()
+    A, Z = W.tridiag(3000, 12)
+    cb = b.cpu_baseline(A, Z, "tridiag_m3000_n12")
+    assert cb["kind"] == "oracle" and cb["unit"] == "QR/s" and cb["value"] > 0
+    assert cb["cores"] >= 1 and str(cb["cores"]) in cb["sample"]
+    st = cb["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and st["kind"] == "oracle"
 
 
 def test_reference_batched_and_served():

@@ -140,28 +140,38 @@ __device__ __forceinline__ void fused_pass(int i, int jbeg, int ncols, int kg, i
     const int rbeg = (u - jr * nb) * 32 + lane;
     int rend = (uend - jr * nb) * 32;
     if (rend > crows) rend = crows;
-    // kTripRows rows per lane per trip: every load of the trip is issued
-    // before its arithmetic, so each lane keeps that many requests in flight.
-    for (int r = rbeg; r < rend; r += 32 * kTripRows) {
-      double z[kTripRows], x[kTripRows];
+    // kTripRows rows per lane per trip.  Software-pipelined: as soon as row q
+    // of a trip is done, the register that held it is reloaded with row q of
+    // the next trip, so the next trip's loads are in flight while the rest of
+    // this trip's FMAs run (the warps of a CTA move through the pass nearly in
+    // lockstep, so loads issued only at the top of a trip would leave the
+    // FP64 pipe idle for a memory latency per trip).  Same operations, same
+    // order as one trip at a time.
+    double z[kTripRows], x[kTripRows];
 #pragma unroll
-      for (int q = 0; q < kTripRows; ++q) {
-        const int rr = r + 32 * q;
-        z[q] = rr < rend ? zc[rr] : 0.0;
-        x[q] = (V == kHP && i > 0 && rr < rend) ? xc[rr] : 0.0;
-      }
+    for (int q = 0; q < kTripRows; ++q) {
+      const int rr = rbeg + 32 * q;
+      z[q] = rr < rend ? zc[rr] : 0.0;
+      x[q] = (V == kHP && i > 0 && rr < rend) ? xc[rr] : 0.0;
+    }
+    for (int r = rbeg; r < rend; r += 32 * kTripRows) {
+      const int rn = r + 32 * kTripRows;  // next trip
 #pragma unroll
       for (int q = 0; q < kTripRows; ++q) {
         const int rr = r + 32 * q;
         if (rr < rend) {
+          double zq = z[q];
           if (i > 0) {
-            z[q] = fma(-rp, s_qprev[rr], z[q]);
-            zc[rr] = z[q];
+            zq = fma(-rp, s_qprev[rr], zq);
+            zc[rr] = zq;
             if (V == kHP) xc[rr] = fma(-rp, s_pprev[rr], x[q]);
           }
-          if (q & 1) acc1 = fma(s_pcur[rr], z[q], acc1);
-          else acc0 = fma(s_pcur[rr], z[q], acc0);
+          if (q & 1) acc1 = fma(s_pcur[rr], zq, acc1);
+          else acc0 = fma(s_pcur[rr], zq, acc0);
         }
+        const int rq = rn + 32 * q;
+        z[q] = rq < rend ? zc[rq] : 0.0;
+        x[q] = (V == kHP && i > 0 && rq < rend) ? xc[rq] : 0.0;
       }
     }
     const double acc = warp_sum(acc0 + acc1);

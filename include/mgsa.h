@@ -252,6 +252,57 @@ size_t mgsa_job_workspace_bytes(int64_t m, int n, mgsa_variant v);
  * count < 0 or NULL arrays (count > 0); count == 0 does nothing. */
 mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, int* info_dev, mgsa_stream_t s);
 
+/* ---------------------------------------------------------------------- */
+/* Grouped launch: several QRs side by side on disjoint gangs of CTAs.      */
+/* ---------------------------------------------------------------------- */
+
+/* One member of a grouped launch: steps [first, first + count) of one QR (a
+ * time slice, as for mgsa_qr_steps) on a gang of `ctas` CTAs of its own.
+ *
+ *   job    A, Z, Q, R, m, n, ld* as for mgsa_qr_batched (device pointers owned
+ *          by the caller); job.variant must be the launch's variant.
+ *          job.work: the member's workspace, mgsa_group_workspace_bytes(h, m,
+ *          n, v) bytes of device memory, 256-byte aligned.  It carries the
+ *          QR's state (x / p columns) between slices, with Q and R, so it and
+ *          they must stay untouched between the slices of one QR.  Its first
+ *          two int32 are the member's outcome once its last slice has run:
+ *          status (0, 2 breakdown, 3 not finite, 6 timeout) and the 1-based
+ *          column, as mgsa_copy_info reports them.
+ *   ctas   CTAs asked for (>= 1); the gang uses at most that many, and fewer
+ *          when the slabs would fall below the smallest slab size (128 rows,
+ *          or MGSA_PARAM_MIN_ROWS_PER_CTA).  A member's results equal those of
+ *          mgsa_qr / mgsa_qr_steps with MGSA_PARAM_MAX_CTAS = ctas and
+ *          MGSA_PARAM_CLUSTER = 1 on a handle with the same settings, bit for
+ *          bit, whatever else runs in the launch.  Slices of one QR may use
+ *          different gang sizes (the last bits then depend on them).
+ *   reserved  0. */
+typedef struct {
+  mgsa_job job;
+  int32_t first;
+  int32_t count;
+  int32_t ctas;
+  int32_t reserved;
+} mgsa_group_member;
+
+/* Most members of one grouped launch. */
+#define MGSA_GROUP_MAX 64
+
+/* Device workspace bytes of one member of a grouped launch on h's device. */
+size_t mgsa_group_workspace_bytes(mgsa_handle h, int64_t m, int n, mgsa_variant v);
+
+/* Grouped launch (Section 1, eq. (1); Algorithms 4, 7, 8, right-looking): one
+ * cooperative launch runs `count` members (a HOST array, read before the call
+ * returns), member k on CTAs of its own, with device-wide barriers that count
+ * only its own gang, so QRs of very different sizes share the GPU without
+ * waiting for each other.  The gangs' CTAs together may not exceed the number
+ * the GPU holds at once (one per SM on GB300).  A slice after a failed slice
+ * of the same QR does nothing.  MGS forms only; the CTA sum, sizes and
+ * pointers are checked on the host (MGSA_ERR_INVALID).  Queues two launches on
+ * s (a reset of the members' barrier words, then the grouped kernel) and
+ * returns; allocates nothing. */
+mgsa_status mgsa_qr_group(mgsa_handle h, mgsa_variant v, int count, const mgsa_group_member* members,
+                          mgsa_stream_t s);
+
 /* Launch parameters (0 restores the default).
  *   MGSA_PARAM_MAX_CTAS          cap on the number of CTAs of a single-instance
  *                                launch (default: one per SM that fits, i.e.

@@ -463,6 +463,98 @@ mgsa_status mgsa_qr_batched(mgsa_handle h, int count, const mgsa_job* jobs_dev, 
   return MGSA_OK;
 }
 
+// Grouped launch: per-CTA partials reserved for the most CTAs the device can
+// ever hold at once (the smallest shared-memory footprint), so that a member
+// may get a different gang size in each slice and its X columns sit at the
+// same place in its workspace whatever the launch.
+static int group_part_ctas(int* max_ctas) {
+  int mc = 0;
+  if (mgsa::group_max_ctas((int)MGSA_HP, mgsa::sweep_smem_bytes(1, 32), &mc) != cudaSuccess || mc < 1) return 0;
+  *max_ctas = mc;
+  return mc;
+}
+
+size_t mgsa_group_workspace_bytes(mgsa_handle h, int64_t m, int n, mgsa_variant v) {
+  if (!h || m < 1 || n < 1 || n > MGSA_MAX_N || (v != MGSA_NAIVE && v != MGSA_HA && v != MGSA_HP)) return 0;
+  DeviceGuard g(h->device);
+  int mc = 0;
+  if (!group_part_ctas(&mc)) return 0;
+  const int64_t cols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
+  return (size_t)mgsa::kGroupCtlBytes +
+         (size_t)round_up(8 * mgsa::group_part_doubles(n, mc), 256) + sizeof(double) * (size_t)round_up(m, 32) * (size_t)cols;
+}
+
+mgsa_status mgsa_qr_group(mgsa_handle h, mgsa_variant v, int count, const mgsa_group_member* members,
+                          mgsa_stream_t s) {
+  if (!h) return fail(MGSA_ERR_INVALID, "NULL handle");
+  if (v != MGSA_NAIVE && v != MGSA_HA && v != MGSA_HP) return fail(MGSA_ERR_INVALID, "grouped launches take MGS forms only");
+  if (count < 1 || count > MGSA_GROUP_MAX) return fail(MGSA_ERR_INVALID, "count must be in [1, MGSA_GROUP_MAX]");
+  if (!members) return fail(MGSA_ERR_INVALID, "NULL member array");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(MGSA_ERR_CUDA, "cannot select the device");
+  int max_n = 1;
+  for (int k = 0; k < count; ++k) max_n = std::max(max_n, (int)members[k].job.n);
+  if (max_n > MGSA_MAX_N) return fail(MGSA_ERR_INVALID, "n must be in [1, MGSA_MAX_N]");
+  int mc = 0;
+  if (!group_part_ctas(&mc)) return fail(MGSA_ERR_CUDA, "sweep kernel does not fit on this device");
+  const int chunk_cap = h->chunk_rows > 0 ? h->chunk_rows : mgsa::kMaxChunk;
+  static_assert(sizeof(mgsa::GroupArgs) <= 16 * 1024, "grouped launch arguments too large");
+  mgsa::GroupArgs* ga = new (std::nothrow) mgsa::GroupArgs();
+  if (!ga) return fail(MGSA_ERR_NOMEM, "host allocation failed");
+  ga->count = count;
+  ga->spmm_panel = h->spmm_panel;
+  int total = 0, chunk_max = 32;
+  mgsa_status st = MGSA_OK;
+  for (int k = 0; k < count && st == MGSA_OK; ++k) {
+    const mgsa_group_member& M = members[k];
+    const mgsa_job& J = M.job;
+    if (J.variant != (int)v) st = fail(MGSA_ERR_INVALID, "a member's variant differs from the launch's");
+    else if (check_sizes(J.m, J.n, J.ldz, v, J.ldq, (int)std::min<int64_t>(J.ldr, INT32_MAX)) != MGSA_OK) st = MGSA_ERR_INVALID;
+    else if (!J.rowptr || !J.Z || !J.Q || !J.R || !J.work) st = fail(MGSA_ERR_INVALID, "NULL member pointer");
+    else if ((reinterpret_cast<uintptr_t>(J.work) & 255) != 0) st = fail(MGSA_ERR_INVALID, "member workspace not 256-byte aligned");
+    else if (M.first < 0 || M.count < 1 || M.first >= J.n || M.count > J.n - M.first)
+      st = fail(MGSA_ERR_INVALID, "member steps [first, first + count) must lie in [0, n)");
+    else if (M.ctas < 1) st = fail(MGSA_ERR_INVALID, "member ctas must be >= 1");
+    for (int k2 = 0; k2 < k && st == MGSA_OK; ++k2)
+      if (members[k2].job.work == J.work || members[k2].job.Q == J.Q || members[k2].job.R == J.R)
+        st = fail(MGSA_ERR_INVALID, "two members share a workspace, Q or R");
+    if (st != MGSA_OK) break;
+    // The plan mgsa_qr would choose with MGSA_PARAM_MAX_CTAS = ctas and no
+    // cluster.  The host does not read A, so the smallest slab is
+    // kMinRowsPerCta unless the row mode says the rows are long; with the
+    // automatic row mode the kernel reads nnz = rowptr[m] to pick the MV form.
+    const bool long_rows = h->row_mode == 2;
+    const int64_t min_rows = h->min_rows > 0 ? h->min_rows : (long_rows ? mgsa::kMinRowsLongRows : mgsa::kMinRowsPerCta);
+    int64_t gk = std::min<int64_t>({(int64_t)M.ctas, (int64_t)mc, (J.m + min_rows - 1) / min_rows});
+    gk = std::max<int64_t>(gk, 1);
+    const int64_t rpc = round_up((J.m + gk - 1) / gk, 32);
+    mgsa::GroupMember& D = ga->members[k];
+    std::memcpy(&D.job, &J, sizeof(mgsa::BatchJob));
+    D.first = M.first;
+    D.count = M.count;
+    D.rpc = (int)rpc;
+    D.G = (int)((J.m + rpc - 1) / rpc);
+    D.chunk = (int)std::min<int64_t>(chunk_cap, rpc);
+    D.mv_warp = h->row_mode == 0 ? -1 : (h->row_mode == 2 ? 1 : 0);
+    D.part_doubles = round_up(8 * mgsa::group_part_doubles(J.n, mc), 256) / 8;
+    ga->offsets[k] = total;
+    total += D.G;
+    chunk_max = std::max(chunk_max, D.chunk);
+  }
+  const size_t smem = mgsa::sweep_smem_bytes(max_n, chunk_max);
+  int cap = 0;
+  if (st == MGSA_OK && mgsa::group_max_ctas((int)v, smem, &cap) != cudaSuccess)
+    st = fail(MGSA_ERR_CUDA, "occupancy query failed");
+  if (st == MGSA_OK && total > cap) st = fail(MGSA_ERR_INVALID, "the members' CTAs exceed what the GPU holds at once");
+  if (st == MGSA_OK) {
+    ga->offsets[count] = total;
+    cudaError_t e = mgsa::group_launch((int)v, *ga, smem, reinterpret_cast<cudaStream_t>(s));
+    if (e != cudaSuccess) st = cuda_fail(e);
+  }
+  delete ga;
+  return st;
+}
+
 mgsa_status mgsa_copy_info(mgsa_handle h, int* info_dev, mgsa_stream_t s) {
   if (!h || !info_dev) return fail(MGSA_ERR_INVALID, "NULL handle or info_dev");
   DeviceGuard g(h->device);

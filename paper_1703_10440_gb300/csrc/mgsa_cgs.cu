@@ -503,9 +503,9 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
     if (V == kHP) {
       sl = block_sum(sl, s_buf);
       if (tid == 0) part_norm[b] = sl;
-      if (!sync_all<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+      if (!sync_all<false>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
     } else {
-      if (!sync_all<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);  // z_j complete in W
+      if (!sync_all<false>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);  // z_j complete in W
       CGS_TRACE(j, 2);
       sl = mv_rows(rowptr, colidx, val, W, 1.0, false, k0, k1, resident, warp_rows, xr, zr, XS, s_xtmp, true);
       sl = block_sum(sl, s_buf);
@@ -514,7 +514,7 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
       sync_arrive<false>(a.ctl, gen, s_flags);
       // r_{i,j+1}, i < j: their partials were stored before the previous wait.
       if (has_next && j > 0) sum_assigned(part_cur, G, n, j, R, ldr, b);
-      if (!sync_wait<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+      if (!sync_wait<false>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
     }
     CGS_TRACE(j, 4);
     // HP: r_{i,j+1}, i < j (partials stored before the norm wait), while warp 0
@@ -571,7 +571,7 @@ __device__ int cgs_body(const SweepArgs& a, const int G, const int b, double* sm
     CGS_TRACE(j, 7);
 
     // ---------------- r_{:,j+1} ----------------
-    if (!sync_all<false>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+    if (!sync_all<false>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
     CGS_TRACE(j, 8);
     if (tid < 32) {
       const double r = warp0_sum_ctas(part_cur + j, n, G);

@@ -66,7 +66,8 @@ __device__ void set_status(int* ctl, int code, int column) {
 // Device-wide barrier for a cooperative launch, in two halves so that a CTA
 // can do independent work between arriving and waiting.  The counter only
 // grows during a launch (it is zeroed before each launch): barrier number k
-// (k = 1, 2, ...) is passed once it reaches k * gridDim.x.  Arrival is a
+// (k = 1, 2, ...) is passed once it reaches k times the number of CTAs that
+// take part (the grid, or one gang of CTAs of a grouped launch).  Arrival is a
 // fire-and-forget release reduction; every CTA then polls the counter with
 // acquire loads.  Only thread 0 of a CTA touches it; `gen` (the number of
 // barriers passed) is meaningful in thread 0 only.
@@ -81,12 +82,12 @@ __device__ __forceinline__ void grid_arrive(int* ctl, unsigned int gen, int* s_u
 }
 
 // Returns false if the wait ran past kSpinLimitNs or another CTA already
-// recorded a failure (then every CTA leaves the kernel).
-__device__ bool grid_wait(int* ctl, unsigned int& gen, const int* s_unused, int* s_ok) {
-  (void)s_unused;
+// recorded a failure (then every CTA leaves the kernel).  `nctas`: the CTAs
+// that arrive at this barrier (the whole grid, or one gang of a grouped launch).
+__device__ bool grid_wait(int* ctl, unsigned int& gen, unsigned int nctas, int* s_ok) {
   if (threadIdx.x == 0) {
     const unsigned int* count = reinterpret_cast<const unsigned int*>(&ctl[kCtlBarCount]);
-    const unsigned int target = (gen + 1u) * gridDim.x;
+    const unsigned int target = (gen + 1u) * nctas;
     int ok = 1;
     if (ld_acquire_u32(count) < target) {
       const unsigned long long t0 = global_timer_ns();
@@ -109,9 +110,9 @@ __device__ bool grid_wait(int* ctl, unsigned int& gen, const int* s_unused, int*
   return *s_ok != 0;
 }
 
-__device__ __forceinline__ bool grid_sync(int* ctl, unsigned int& gen, int* s_flags) {
+__device__ __forceinline__ bool grid_sync(int* ctl, unsigned int& gen, unsigned int nctas, int* s_flags) {
   grid_arrive(ctl, gen, s_flags);
-  return grid_wait(ctl, gen, s_flags, s_flags + 1);
+  return grid_wait(ctl, gen, nctas, s_flags + 1);
 }
 
 // Hardware barrier of a thread-block cluster: every thread of every CTA of
@@ -136,8 +137,10 @@ __device__ __forceinline__ void sync_arrive(int* ctl, unsigned int gen, int* s_f
   else grid_arrive(ctl, gen, s_flags);
 }
 
+// `nctas`: CTAs taking part in a device-wide barrier (unused for the CTA and
+// cluster forms).
 template <bool kBatch, bool kCluster = false>
-__device__ __forceinline__ bool sync_wait(int* ctl, unsigned int& gen, int* s_flags) {
+__device__ __forceinline__ bool sync_wait(int* ctl, unsigned int& gen, unsigned int nctas, int* s_flags) {
   if (kCluster) {
     cluster_wait();
     return true;
@@ -146,13 +149,13 @@ __device__ __forceinline__ bool sync_wait(int* ctl, unsigned int& gen, int* s_fl
     __syncthreads();
     return true;
   }
-  return grid_wait(ctl, gen, s_flags, s_flags + 1);
+  return grid_wait(ctl, gen, nctas, s_flags + 1);
 }
 
 template <bool kBatch, bool kCluster = false>
-__device__ __forceinline__ bool sync_all(int* ctl, unsigned int& gen, int* s_flags) {
+__device__ __forceinline__ bool sync_all(int* ctl, unsigned int& gen, unsigned int nctas, int* s_flags) {
   sync_arrive<kBatch, kCluster>(ctl, gen, s_flags);
-  return sync_wait<kBatch, kCluster>(ctl, gen, s_flags);
+  return sync_wait<kBatch, kCluster>(ctl, gen, nctas, s_flags);
 }
 
 // Result of the step body: 0, or (device status << 24) | 1-based column.
@@ -240,24 +243,33 @@ __device__ void reduce_range(const double* part, int G, int stride, int jbeg, in
 constexpr int kResRows = kMaxChunk / kThreads;  // rows per thread when a CTA's slab is one chunk
 
 // out[q] = sum_e val[e] * (scale_src ? src[col[e]] * scale : src[col[e]]) for
-// the rows k + q*kThreads (q < 4) below k1, each summed in stored order.  The
-// four rows advance in lockstep so their gathers are in flight together.
-__device__ __forceinline__ void csr_rows4(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                          const double* __restrict__ val, const double* src, double scale,
-                                          bool scale_src, int64_t k, int64_t k1, double out[4]) {
-  int e[4], e1[4];
+// the rows k + q*kThreads (q < kRows) below k1, each summed in stored order.
+// The kRows rows advance in lockstep so that their gathers are in flight
+// together (each entry is two dependent loads: the column index, then the
+// gathered value).  kL1: gather through L1 (only for a source vector this SM
+// has not read earlier in the launch at the gathered addresses), else from L2.
+template <int kRows, bool kL1 = false>
+__device__ __forceinline__ void csr_rows(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                         const double* __restrict__ val, const double* src, double scale,
+                                         bool scale_src, int64_t k, int64_t k1, double out[kRows]) {
+  int e[kRows], e1[kRows];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < kRows; ++q) {
     const int64_t kk = k + q * kThreads;
     e[q] = kk < k1 ? __ldg(rowptr + kk) : 0;
     e1[q] = kk < k1 ? __ldg(rowptr + kk + 1) : 0;
     out[q] = 0.0;
   }
-  while (e[0] < e1[0] || e[1] < e1[1] || e[2] < e1[2] || e[3] < e1[3]) {
+  for (;;) {
+    bool any = false;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kRows; ++q) any |= e[q] < e1[q];
+    if (!any) break;
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
       if (e[q] < e1[q]) {
-        const double zv = ld_cg(src + __ldg(colidx + e[q]));
+        const double* g = src + __ldg(colidx + e[q]);
+        const double zv = kL1 ? __ldca(g) : ld_cg(g);
         out[q] = fma(__ldg(val + e[q]), scale_src ? zv * scale : zv, out[q]);
         ++e[q];
       }
@@ -265,9 +277,17 @@ __device__ __forceinline__ void csr_rows4(const int32_t* __restrict__ rowptr, co
   }
 }
 
+__device__ __forceinline__ void csr_rows4(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                          const double* __restrict__ val, const double* src, double scale,
+                                          bool scale_src, int64_t k, int64_t k1, double out[4]) {
+  csr_rows<4>(rowptr, colidx, val, src, scale, scale_src, k, k1, out);
+}
+
 // Long rows: one warp per row.  Lane l takes the entries e0 + l, e0 + l + 32,
 // ... (coalesced column and value loads), two accumulators, then a butterfly;
-// every lane returns the row's sum (a fixed tree, so deterministic).
+// every lane returns the row's sum (a fixed tree, so deterministic).  kL1 as
+// for csr_rows.
+template <bool kL1 = false>
 __device__ __forceinline__ double csr_row_warp(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                                const double* __restrict__ val, const double* src, double scale,
                                                bool scale_src, int64_t k) {
@@ -276,13 +296,16 @@ __device__ __forceinline__ double csr_row_warp(const int32_t* __restrict__ rowpt
   double acc0 = 0.0, acc1 = 0.0;
   int e = e0 + lane;
   for (; e + 32 < e1; e += 64) {
-    const double g0 = ld_cg(src + __ldg(colidx + e));
-    const double g1 = ld_cg(src + __ldg(colidx + e + 32));
+    const double* a0 = src + __ldg(colidx + e);
+    const double* a1 = src + __ldg(colidx + e + 32);
+    const double g0 = kL1 ? __ldca(a0) : ld_cg(a0);
+    const double g1 = kL1 ? __ldca(a1) : ld_cg(a1);
     acc0 = fma(__ldg(val + e), scale_src ? g0 * scale : g0, acc0);
     acc1 = fma(__ldg(val + e + 32), scale_src ? g1 * scale : g1, acc1);
   }
   if (e < e1) {
-    const double g0 = ld_cg(src + __ldg(colidx + e));
+    const double* a0 = src + __ldg(colidx + e);
+    const double g0 = kL1 ? __ldca(a0) : ld_cg(a0);
     acc0 = fma(__ldg(val + e), scale_src ? g0 * scale : g0, acc0);
   }
   return warp_sum(acc0 + acc1);

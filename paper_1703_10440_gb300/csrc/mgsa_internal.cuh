@@ -106,6 +106,32 @@ struct BatchArgs {
   int spmm_panel = 8;      // as SweepArgs::spmm_panel, for every HP job
 };
 
+// Grouped launch: up to kGroupMax QRs side by side in one cooperative launch,
+// each on a gang of CTAs of its own with its own device-wide barrier, each
+// running a step range (a time slice) of its loop.
+constexpr int kGroupMax = 64;
+constexpr int kGroupCtlBytes = 256;  // member workspace: [ctl][partials][X columns]
+
+struct GroupMember {
+  BatchJob job;    // A, Z, Q, R, sizes; work = the member's workspace
+  int first;       // steps [first, first + count) run in this launch
+  int count;
+  int G;           // CTAs of the gang
+  int rpc;         // rows per CTA (multiple of 32)
+  int chunk;       // rows per staged pivot chunk
+  int mv_warp;     // one warp per CSR row in the MVs / block product (-1: decide from nnz = rowptr[m])
+  int64_t part_doubles;  // per-CTA partial sums in the workspace
+};
+
+struct GroupArgs {
+  int count;
+  int spmm_panel;
+  int offsets[kGroupMax + 1];  // first CTA of member k; offsets[count] = the grid
+  GroupMember members[kGroupMax];
+};
+
+inline int64_t group_part_doubles(int n, int G) { return (int64_t)(2 * n + 1) * G; }
+
 // Records the message mgsa_last_error returns on this thread (mgsa_api.cu).
 void set_last_error(const char* why);
 
@@ -113,6 +139,8 @@ void set_last_error(const char* why);
 cudaError_t sweep_prepare(int device);  // sets shared-memory attributes once per device
 cudaError_t sweep_max_ctas(int variant, size_t smem, int* max_ctas);
 cudaError_t sweep_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t group_max_ctas(int variant, size_t smem, int* max_ctas);
+cudaError_t group_launch(int variant, const GroupArgs& ga, size_t smem, cudaStream_t s);
 
 // One instance on one thread-block cluster of up to kMaxClusterCtas CTAs
 // (non-portable sizes above 8 allowed where the GPU takes them).

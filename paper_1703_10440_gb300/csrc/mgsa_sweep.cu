@@ -105,6 +105,14 @@ __device__ __forceinline__ void reload_row(const double* R, int ldr, int kg, int
 }
 
 constexpr int kTripRows = 8;                     // rows per lane per trip of the fused pass
+constexpr int kMvRows = 4;                       // rows per thread in lockstep in the MVs of a staged slab (8, 16: slower)
+// The first MV of a step (x_i = A z_i) gathers z_i through L1.  Safe: no CTA
+// reads another CTA's rows of column i before this MV (the fused passes and
+// the L update touch only a CTA's own rows, and slabs start on 256-byte
+// boundaries, so no cache line holds rows of two slabs), so no stale line of
+// those addresses can sit in this SM's L1.  Naive's second MV gathers q_i from
+// the same addresses after they were rewritten and therefore reads L2.
+constexpr bool kMvGatherL1 = true;
 
 // The fused pass over one chunk of rows [c0, c0 + crows) and the columns
 // j = jbeg .. jbeg+ncols-1: apply step i-1's updates z_j -= r_{i-1,j} q_{i-1} (HP:
@@ -362,7 +370,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       sync_arrive<kBatch, kCluster>(a.ctl, gen, s_flags);
       if (!kDist && rest_prev)  // r_{i-1,j}, j > i
         reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
-      if (!sync_wait<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+      if (!sync_wait<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
     } else {
       const double* zsrc;  // column i of the working Z, complete on every row
       if (i > 0) {
@@ -404,7 +412,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         if (!kDist && rest_prev)
           reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
         MGSA_TRACE(i, 11);
-        if (!sync_wait<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+        if (!sync_wait<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
         MGSA_TRACE(i, 12);
         zsrc = zi;
       } else {
@@ -426,7 +434,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         const int lane = tid & 31, warp = tid >> 5;
         double* xtmp = s_piv + (2 * cur + 1) * chunk;
         for (int64_t k = k0 + warp; k < k1; k += kWarps) {
-          const double x = csr_row_warp(rowptr, colidx, val, zsrc, 1.0, false, k);
+          const double x = csr_row_warp<kMvGatherL1>(rowptr, colidx, val, zsrc, 1.0, false, k);
           if (lane == 0) {
             if (resident) {
               xtmp[k - k0] = x;
@@ -449,7 +457,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
 #pragma unroll
         for (int h = 0; h < kResRows / 4; ++h) {
           double xv[4];
-          csr_rows4(rowptr, colidx, val, zsrc, 1.0, false, k0 + tid + (int64_t)h * 4 * kThreads, k1, xv);
+          csr_rows<4, kMvGatherL1>(rowptr, colidx, val, zsrc, 1.0, false, k0 + tid + (int64_t)h * 4 * kThreads, k1, xv);
 #pragma unroll
           for (int q = 0; q < 4; ++q) xr[4 * h + q] = xv[q];
         }
@@ -457,16 +465,16 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         for (int t = 0; t < kResRows; ++t)
           if (tid + t * kThreads < crows_all) sl = fma(zr[t], xr[t], sl);
       } else {
-        for (int64_t k = k0 + tid; k < k1; k += 4 * kThreads) {
-          double xv[4], zk[4];
-          csr_rows4(rowptr, colidx, val, zsrc, 1.0, false, k, k1, xv);
+        for (int64_t k = k0 + tid; k < k1; k += kMvRows * kThreads) {
+          double xv[kMvRows], zk[kMvRows];
+          csr_rows<kMvRows, kMvGatherL1>(rowptr, colidx, val, zsrc, 1.0, false, k, k1, xv);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < kMvRows; ++q) {
             const int64_t kk = k + q * kThreads;
             zk[q] = kk < k1 ? ld_cg(zsrc + kk) : 0.0;
           }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < kMvRows; ++q) {
             const int64_t kk = k + q * kThreads;
             if (kk < k1) {
               X[kk] = xv[q];
@@ -478,7 +486,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       sl = block_sum(sl, s_buf);
       if (tid == 0) part_norm[b] = sl;
       MGSA_TRACE(i, 1);
-      if (!sync_all<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+      if (!sync_all<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
     }
     MGSA_TRACE(i, 2);
     if (kDist && rest_prev) reload_row(R, ldr, kg, i, nt, s_rrow);  // r_{i-1,j}, j > i
@@ -497,7 +505,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         const int rr = tid + t * kThreads;
         if (rr < crows_all) zi[k0 + rr] = zr[t] * inv;
       }
-      if (!sync_all<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+      if (!sync_all<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
       if (a.mv_warp) {
         const int lane = tid & 31, warp = tid >> 5;
         double* ptmp = s_piv + (2 * cur + 1) * chunk;
@@ -529,18 +537,18 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
           if ((tid & 31) == 0) X[k + ldx] = pk;
         }
       } else {
-        for (int64_t k = k0 + tid; k < k1; k += 4 * kThreads) {
-          double pv[4];
-          csr_rows4(rowptr, colidx, val, zsrc, inv, true, k, k1, pv);
+        for (int64_t k = k0 + tid; k < k1; k += kMvRows * kThreads) {
+          double pv[kMvRows];
+          csr_rows<kMvRows>(rowptr, colidx, val, zsrc, inv, true, k, k1, pv);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < kMvRows; ++q) {
             const int64_t kk = k + q * kThreads;
             if (kk < k1) X[kk + ldx] = pv[q];
           }
         }
       }
       // Other CTAs still gather z_i; q_i may overwrite it only after this wait.
-      if (!sync_all<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+      if (!sync_all<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
     }
     }  // !given
 
@@ -642,7 +650,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     if (ncols == 0) break;
     for (int jr = tid; jr < ncols; jr += kThreads) part_cur[(int64_t)b * nt + (jbeg + jr)] = s_racc[jr];
     MGSA_TRACE(i, 7);
-    if (!sync_all<kBatch, kCluster>(a.ctl, gen, s_flags)) return body_result(kDevTimeout, 0);
+    if (!sync_all<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
     MGSA_TRACE(i, 8);
     if (given) {
       reduce_range(part_cur, G, nt, jbeg, nt, s_rrow, s_buf, b == 0 ? R + i : nullptr, ldr, kg);  // all of row i
@@ -669,6 +677,63 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_sweep_kernel(const SweepArgs 
   // Breakdown verdicts are identical in every CTA; CTA 0 records them.  A
   // timeout was recorded by the CTA that saw it.
   if (r != 0 && (r >> 24) != kDevTimeout && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.ctl, r >> 24, r & 0xFFFFFF);
+}
+
+// Several instances side by side in one cooperative launch (a grouped launch):
+// member k owns CTAs [offsets[k], offsets[k+1]) -- its gang -- and runs steps
+// [first, first + count) of its loop over them with the time-slice body, its
+// device-wide barriers counting only its own G CTAs on its own control words.
+// No CTA waits for another member's, so members of any sizes share the GPU.
+// For the same G, rows per CTA and chunk a member computes what mgsa_qr_steps
+// computes with that plan, bit for bit.
+template <int V, int kPanel>
+__global__ void __launch_bounds__(kThreads, 1) mgs_group_kernel(const __grid_constant__ GroupArgs ga) {
+  extern __shared__ __align__(16) double smem[];
+  __shared__ int s_wfirst[kWarps], s_wlast[kWarps];
+  __shared__ int s_flags[2];
+  int k = 0;
+  while (k + 1 < ga.count && (int)blockIdx.x >= ga.offsets[k + 1]) ++k;
+  const GroupMember& M = ga.members[k];
+  const int b = (int)blockIdx.x - ga.offsets[k];
+  unsigned char* work = reinterpret_cast<unsigned char*>(M.job.work);
+  SweepArgs a;
+  a.m = M.job.m;
+  a.n = M.job.n;
+  a.rowptr = M.job.rowptr;
+  a.col = M.job.col;
+  a.val = M.job.val;
+  a.Z = M.job.Z;
+  a.ldz = M.job.ldz;
+  a.Q = M.job.Q;
+  a.ldq = M.job.ldq;
+  a.R = M.job.R;
+  a.ldr = (int)M.job.ldr;
+  a.ctl = reinterpret_cast<int*>(work);
+  a.part = reinterpret_cast<double*>(work + kGroupCtlBytes);
+  a.X = a.part + M.part_doubles;
+  a.ldx = (M.job.m + 31) / 32 * 32;
+  a.rpc = M.rpc;
+  a.chunk = M.chunk;
+  a.mv_warp = M.mv_warp >= 0 ? M.mv_warp : (int64_t)__ldg(M.job.rowptr + M.job.m) >= (int64_t)kWarpRowNnz * M.job.m;
+  a.spmm_panel = kPanel;
+  a.step_begin = M.first;
+  a.step_end = M.first + M.count;
+  const int r = sweep_body<V, false, kPanel, true>(a, M.G, b, smem, s_wfirst, s_wlast, s_flags);
+  if (r != 0 && (r >> 24) != kDevTimeout && b == 0 && threadIdx.x == 0) set_status(a.ctl, r >> 24, r & 0xFFFFFF);
+}
+
+// Before a grouped launch: every member's barrier counter starts at zero, and
+// a member's first slice clears its status word too.
+__global__ void group_reset_kernel(const __grid_constant__ GroupArgs ga) {
+  for (int k = threadIdx.x; k < ga.count; k += blockDim.x) {
+    int* ctl = reinterpret_cast<int*>(ga.members[k].job.work);
+    ctl[kCtlBarCount] = 0;
+    ctl[kCtlBarGen] = 0;
+    if (ga.members[k].first == 0) {
+      ctl[kCtlStatus] = 0;
+      ctl[kCtlColumn] = 0;
+    }
+  }
 }
 
 // Single instance on one thread-block cluster (the whole grid): the same loop
@@ -775,13 +840,22 @@ static const void* batch_fn(int variant, int panel = 8) {
 // Every kernel instance: (variant, panel width).
 static const int kKernelInstances[4][2] = {{kNaive, 8}, {kHA, 8}, {kHP, 8}, {kHP, 4}};
 
+static const void* group_fn(int variant, int panel = 8) {
+  switch (variant) {
+    case kNaive: return reinterpret_cast<const void*>(mgs_group_kernel<kNaive, 8>);
+    case kHA: return reinterpret_cast<const void*>(mgs_group_kernel<kHA, 8>);
+    default:
+      return panel == 4 ? reinterpret_cast<const void*>(mgs_group_kernel<kHP, 4>)
+                        : reinterpret_cast<const void*>(mgs_group_kernel<kHP, 8>);
+  }
+}
+
 cudaError_t sweep_prepare(int device) {
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e != cudaSuccess) return e;
   for (const auto& k : kKernelInstances) {
-    for (const bool sliced : {false, true}) {
-      const void* fn = sweep_fn(k[0], k[1], sliced);
+    for (const void* fn : {sweep_fn(k[0], k[1], false), sweep_fn(k[0], k[1], true), group_fn(k[0], k[1])}) {
       cudaFuncAttributes fa;
       if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
       const int dyn = optin - (int)fa.sharedSizeBytes;  // static shared memory counts against the opt-in limit
@@ -895,6 +969,26 @@ cudaError_t batch_launch(const BatchArgs& ba, int grid, size_t smem, cudaStream_
   if (ba.spmm_panel == 4) mgs_batch_kernel<kHP, 4><<<grid, kThreads, smem, s>>>(ba);
   else mgs_batch_kernel<kHP, 8><<<grid, kThreads, smem, s>>>(ba);
   return cudaGetLastError();
+}
+
+cudaError_t group_max_ctas(int variant, size_t smem, int* max_ctas) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, group_fn(variant), kThreads, smem)) != cudaSuccess)
+    return e;
+  *max_ctas = sms * per_sm;
+  return cudaSuccess;
+}
+
+cudaError_t group_launch(int variant, const GroupArgs& ga, size_t smem, cudaStream_t s) {
+  group_reset_kernel<<<1, 64, 0, s>>>(ga);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<GroupArgs*>(&ga)};
+  return cudaLaunchCooperativeKernel(group_fn(variant, ga.spmm_panel), dim3(ga.offsets[ga.count]), dim3(kThreads),
+                                     args, smem, s);
 }
 
 cudaError_t sweep_launch(int variant, const SweepArgs& a, int grid, size_t smem, cudaStream_t s) {

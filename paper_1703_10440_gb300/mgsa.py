@@ -46,6 +46,12 @@ class mgsa_job(ctypes.Structure):
                 ("R", ctypes.c_void_p), ("ldr", ctypes.c_int64), ("work", ctypes.c_void_p)]
 
 
+class mgsa_group_member(ctypes.Structure):
+    _fields_ = [("job", mgsa_job), ("first", ctypes.c_int32), ("count", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+MGSA_GROUP_MAX = 64
 MGSA_BATCH_MAX_N = 256
 MGSA_BATCH_INFO_INVALID = -2147483647
 
@@ -79,6 +85,8 @@ SIGNATURES = {
     "mgsa_qr_batched": (_INT, [_VP, _INT, _VP, _VP, _VP]),
     "mgsa_qr_append": (_INT, [_VP, ctypes.POINTER(mgsa_csr), _VP, _I64, _VP, _I64, _INT, _VP, _I64, _INT, _I64, _INT,
                               _VP, _I64, _VP, _I64, _VP, _INT, _VP]),
+    "mgsa_group_workspace_bytes": (_SZ, [_VP, _I64, _INT, _INT]),
+    "mgsa_qr_group": (_INT, [_VP, _INT, _INT, ctypes.POINTER(mgsa_group_member), _VP]),
     "mgsa_fp64_probe": (_INT, [_INT, _INT, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mgsa_last_error": (ctypes.c_char_p, []),
 }
@@ -205,6 +213,24 @@ def mgsa_qr_batched(h: int, count: int, jobs_dev, info_dev, stream=None) -> int:
     """Queue a batch; ``jobs_dev`` is a device buffer holding ``count``
     ``mgsa_job`` structs, ``info_dev`` a device int32 buffer of ``count``."""
     return int(lib().mgsa_qr_batched(h, count, _ptr(jobs_dev), _ptr(info_dev), _stream(stream)))
+
+
+def mgsa_group_workspace_bytes(h: int, m: int, n: int, variant: int) -> int:
+    return int(lib().mgsa_group_workspace_bytes(h, m, n, variant))
+
+
+def mgsa_qr_group(h: int, variant: int, members, stream=None) -> int:
+    """Queue one grouped launch; ``members`` is a sequence of
+    ``mgsa_group_member``; returns the status of the call."""
+    arr = (mgsa_group_member * len(members))(*members)
+    return int(lib().mgsa_qr_group(h, variant, len(members), arr, _stream(stream)))
+
+
+def group_member(m: int, n: int, variant: int, rowptr, col, val, Z, ldz: int, Q, ldq: int, R, ldr: int, work,
+                 first: int, count: int, ctas: int) -> mgsa_group_member:
+    job = mgsa_job(m, n, variant, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(Z), ldz, _ptr(Q), ldq, _ptr(R), ldr,
+                   _ptr(work))
+    return mgsa_group_member(job, first, count, ctas, 0)
 
 
 def mgsa_copy_info(h: int, info_dev, stream=None) -> None:

@@ -69,63 +69,6 @@ namespace {
 constexpr int kGroup = 8;       // pivots whose dot partials one thread carries at once
 constexpr int kPieceCols = 64;  // pivots per flush of the per-warp partial sums
 
-// ---- mbarrier and bulk-copy primitives (PTX ISA: mbarrier, cp.async.bulk) ----
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Waits for the completion of the phase of `bar` with parity `parity`.
-// False once kSpinLimitNs have passed (then *abort is raised for the whole
-// CTA) or as soon as another thread of the CTA has raised *abort.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_timer_ns();
-  for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*abort) return false;
-    if (global_timer_ns() - t0 > kSpinLimitNs) {
-      *abort = 1;
-      return false;
-    }
-  }
-}
-
-// bytes (a multiple of 16, both addresses 16-byte aligned) from global to
-// this CTA's shared memory; completion is counted on `bar`.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-
-// Makes this thread's earlier generic-proxy global stores visible to later
-// bulk copies (async proxy) that read them.
-__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-
 // Sums of v[0..7] over the 32 lanes of a warp: three halving exchanges (lane
 // l keeps the entries selected by its bits 4, 3, 2) leave lane l with the sum
 // of v[(l >> 2) & 7] over 8 lanes; two butterflies complete it.  Lanes with

@@ -6,7 +6,9 @@ calls of ``mgsa_qr`` on one stream, each followed by ``mgsa_get_info``.
 Prints the CUDA-event time of every call.
 
 Usage: python -m paper_1703_10440_gb300.run_once WORKLOAD FORM [REPEATS]
-  WORKLOAD  poisson2d | varcoef3d | tridiag | denseband
+  WORKLOAD  poisson2d | varcoef3d | varcoef3d_64 | tridiag | denseband
+            (varcoef3d_64: the 3D operator on a 64^3 grid with n = 128, an
+            eighth of the rows of varcoef3d: inputs still larger than L2)
   FORM      naive | ha | hp | cgs_naive | cgs_ha | cgs_hp
 """
 from __future__ import annotations
@@ -27,7 +29,8 @@ def main(argv: list[str]) -> None:
 
     from . import mgsa
 
-    gens = {"poisson2d": W.poisson2d, "varcoef3d": W.varcoef3d, "tridiag": lambda: W.tridiag(4096, 16),
+    gens = {"poisson2d": W.poisson2d, "varcoef3d": W.varcoef3d, "varcoef3d_64": lambda: W.varcoef3d(side=64, n=128),
+            "tridiag": lambda: W.tridiag(4096, 16),
             "denseband": W.denseband}
     if which not in gens or form not in mgsa.VARIANTS:
         raise SystemExit(__doc__)

@@ -14,10 +14,16 @@ that asks for many A-orthonormalisations of different sizes.  The server:
   on the device and launches the waiting large request with the least work
   (m * n^2) next, so medium requests overtake queued big ones;
 * with ``slice_ms`` > 0, runs large requests in time slices of about that
-  long (``mgsa_qr_steps``), each request on a handle of its own from a small
-  pool, and picks the slice to launch next by least remaining work, so a
-  request that arrives while a long factorisation runs waits for one slice,
-  not for the whole factorisation;
+  long, so a request that arrives while a long factorisation runs waits for
+  one slice, not for the whole factorisation.  By default
+  (``large_mode="group"``) each launch is one grouped launch
+  (``mgsa_qr_group``): the waiting large requests with the least remaining
+  work share the large part of the GPU side by side, each on a gang of CTAs
+  sized in proportion to its rows, each for a slice of about ``slice_ms``;
+  up to ``max_large_inflight`` such launches are queued on the stream, so the
+  GPU never waits for the host between them.  With ``large_mode="slices"``
+  each slice is a whole-GPU ``mgsa_qr_steps`` launch of one request on a
+  handle of its own from a small pool, least remaining work first;
 * with ``small_ctas`` = k > 0, partitions the SMs: large requests run with
   k fewer CTAs than the GPU has SMs, small ones on a second stream and a
   second handle whose batched launches use k CTAs, so the two kinds run side
@@ -60,6 +66,8 @@ class Request:
     R: object = None
     work: object = None
     nbytes: int = 0
+    need: int = 0            # device bytes the request needs once admitted (computed once)
+    ready: object = None     # event on the generator stream after its inputs were drawn
     small: bool = False
     t_done: float = math.nan
     info: int = -99
@@ -92,7 +100,9 @@ def poisson_arrivals(rate: float, duration: float, seed: int = 20170330, m_lo: f
 class Server:
     def __init__(self, handle: int, variant: str = "hp", budget_bytes: float = 120e9, small_work: float = 2e7,
                  device: int = 0, max_batch: int = 4096, max_m: int = 1_000_000, max_n: int = 128,
-                 small_ctas: int = 0, max_large_inflight: int = 0, slice_ms: float = 0.0, large_handles: int = 3):
+                 small_ctas: int = 0, max_large_inflight: int = 0, slice_ms: float = 0.0, large_handles: int = 3,
+                 large_mode: str = "group", rows_per_cta: int = 4096, admit_per_tick: int = 0,
+                 gang_fill: str = "prefix"):
         import torch
 
         self.torch = torch
@@ -103,6 +113,10 @@ class Server:
         self.small_work = small_work
         self.dev = torch.device("cuda", device)
         self.max_batch = max_batch
+        # Requests admitted per turn of the loop (0: as many as the budget
+        # allows).  Drawing a request's inputs costs the host about a
+        # millisecond; a bounded turn keeps launches flowing under a backlog.
+        self.admit_per_tick = admit_per_tick
         self.stream = torch.cuda.Stream(self.dev)
         self.gen_stream = torch.cuda.Stream(self.dev)
         self.small_ctas = small_ctas
@@ -120,10 +134,20 @@ class Server:
         # Large requests share the handle's workspace: size it once, up front.
         mgsa.mgsa_reserve(handle, max_m, max_n, self.v)
         self.shared_ws = mgsa.mgsa_workspace_bytes(handle, max_m, max_n, self.v)
-        # Sliced large requests: one pool handle per request in progress.
+        # Sliced large requests: grouped launches, or one pool handle per
+        # request in progress.
         self.slice_ms = slice_ms
+        if large_mode not in ("group", "slices"):
+            raise ValueError("large_mode: 'group' or 'slices'")
+        self.group = slice_ms > 0 and large_mode == "group"
+        self.rows_per_cta = rows_per_cta
+        if gang_fill not in ("prefix", "greedy"):
+            raise ValueError("gang_fill: 'prefix' or 'greedy'")
+        self.gang_fill = gang_fill
+        self.sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
+        self.large_ctas = self.sms - max(small_ctas, 0)
         self._pool: list[int] = []
-        if slice_ms > 0:
+        if slice_ms > 0 and not self.group:
             sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
             for _ in range(large_handles):
                 hh = mgsa.mgsa_create(device)
@@ -151,11 +175,13 @@ class Server:
     # Cost model of one step (seconds): the sweep's FP64 work on the remaining
     # columns at an effective 0.8 TFLOP/s, the per-column MVs of HA / naive,
     # and a fixed 20 us of barriers and reductions.
-    def _step_s(self, r: Request, i: int) -> float:
+    # On a gang of c of the GPU's S CTAs the work part scales by S / c.
+    def _step_s(self, r: Request, i: int, ctas: int = 0) -> float:
         per_pair = 6.0 if self.variant == "hp" else 4.0
         nnz_row = 5.0 if r.kind == "laplace" else 17.0
         mvs = 0 if self.variant == "hp" else (2 if self.variant == "naive" else 1)
-        return (per_pair * r.m * (r.n - 1 - i) + mvs * 2.0 * nnz_row * r.m) / 0.8e12 + 20e-6
+        share = 1.0 if ctas <= 0 else self.sms / ctas
+        return share * (per_pair * r.m * (r.n - 1 - i) + mvs * 2.0 * nnz_row * r.m) / 0.8e12 + 20e-6
 
     def _remaining_s(self, r: Request) -> float:
         k = r.n - r.next_step
@@ -189,6 +215,80 @@ class Server:
         r.slice_inflight = True
         return ("slice", [r], done, last)
 
+    # -- grouped launches of large requests ---------------------------------
+    def _gangs(self, cands: list[Request]) -> list[tuple[Request, int]]:
+        """The members of the next grouped launch and their CTAs.  Requests
+        are taken in the given order (least remaining work first), each with
+        the gang it wants or the CTAs still free, until the large part of the
+        GPU is taken; every gang is at least one CTA and at most one CTA per
+        128 rows (the smallest slab).  CTAs left over (members capped by their
+        rows) go to the members with the most rows (with a backlog) or in
+        order (otherwise).
+
+        With a backlog (four or more candidates) a gang wants one CTA per
+        ``rows_per_cta`` rows, for throughput: every member then has about the
+        same rows per CTA, so their slices take about the same time.
+        Otherwise it wants one CTA per ``rows_per_cta // 4`` rows, for
+        latency, and the request closest to done finishes first."""
+        backlog = len(cands) >= 4
+        target = self.rows_per_cta if backlog else max(128, self.rows_per_cta // 4)
+        left = self.large_ctas
+        chosen, ctas, caps = [], [], []
+        for r in cands:
+            if left <= 0 or len(chosen) == mgsa.MGSA_GROUP_MAX:
+                break
+            cap = max(1, -(-r.m // 128))
+            want = max(1, min(cap, -(-r.m // target)))
+            g = min(want, left)
+            if g < want and chosen:
+                if self.gang_fill == "prefix":  # the first request that does not fit ends the group
+                    break
+                # "greedy": a gang squeezed below what the request wants must
+                # still run one step within a slice (a launch lasts as long as
+                # its slowest member), else the request waits.
+                if self._step_s(r, r.next_step, g) > self.slice_ms * 1e-3:
+                    continue
+            chosen.append(r)
+            ctas.append(g)
+            caps.append(cap)
+            left -= g
+        order = sorted(range(len(chosen)), key=lambda k: -chosen[k].m) if backlog else range(len(chosen))
+        for k in order:
+            if left <= 0:
+                break
+            add = min(left, caps[k] - ctas[k])
+            ctas[k] += add
+            left -= add
+        return list(zip(chosen, ctas))
+
+    def _launch_group(self, cands: list[Request]):
+        torch = self.torch
+        members = self._gangs(cands)
+        for r, _ in members:
+            if r.next_step == 0:  # its inputs come from the generator stream
+                self.stream.wait_event(r.ready)
+        specs, finishing = [], []
+        for r, c in members:
+            first, count, t = r.next_step, 0, 0.0
+            while first + count < r.n and (count == 0 or t < self.slice_ms * 1e-3):
+                t += self._step_s(r, first + count, c)
+                count += 1
+            rowptr, col, val = r.A
+            specs.append(mgsa.group_member(r.m, r.n, self.v, rowptr, col, val, r.Z, r.m, r.Q, r.Q.stride(0), r.R, r.n,
+                                           r.work, first, count, c))
+            r.next_step = first + count
+            if r.next_step >= r.n:
+                finishing.append(r)
+        st = mgsa.mgsa_qr_group(self.h, self.v, specs, self.stream)
+        if st != mgsa.MGSA_OK:
+            raise mgsa.MgsaError(st, mgsa.mgsa_last_error())
+        with torch.cuda.stream(self.stream):
+            for r in finishing:  # the member's status words, as mgsa_copy_info reports them
+                r.info_buf.copy_(r.work[:1].view(torch.int32))
+        done = torch.cuda.Event(enable_timing=True)
+        done.record(self.stream)
+        return ("group", finishing, done, len(members))
+
     # -- admission ---------------------------------------------------------
     def _bytes(self, r: Request) -> int:
         m, n = r.m, r.n
@@ -196,6 +296,8 @@ class Server:
         b = 12 * nnz + 4 * (m + 1) + 2 * 8 * m * n + 8 * n * n
         if r.m * r.n ** 2 <= self.small_work:
             b += mgsa.mgsa_job_workspace_bytes(m, n, self.v)
+        elif self.group:
+            b += mgsa.mgsa_group_workspace_bytes(self.h, m, n, self.v)
         return b
 
     def _materialize(self, r: Request):
@@ -211,10 +313,16 @@ class Server:
             if r.small:
                 r.work = torch.empty(mgsa.mgsa_job_workspace_bytes(r.m, r.n, self.v) // 8 + 1, dtype=torch.float64,
                                      device=self.dev)
+            elif self.group:  # x / p columns, partials and status words of its grouped slices
+                r.work = torch.empty(mgsa.mgsa_group_workspace_bytes(self.h, r.m, r.n, self.v) // 8 + 1,
+                                     dtype=torch.float64, device=self.dev)
+                assert r.work.data_ptr() % 256 == 0
             r.info_buf = torch.zeros(2, dtype=torch.int32, device=self.dev)
+            r.ready = torch.cuda.Event()
+            r.ready.record(self.gen_stream)
 
     def _release(self, r: Request):
-        r.A = r.Z = r.Q = r.R = r.work = r.info_buf = None
+        r.A = r.Z = r.Q = r.R = r.work = r.info_buf = r.ready = None
 
     # -- launches ----------------------------------------------------------
     def _launch(self, admitted: list[Request], ref_event):
@@ -276,13 +384,37 @@ class Server:
         t0 = time.perf_counter()
         ticks = launches = 0
         window = self.max_large_inflight if self.max_large_inflight > 0 else 2
+        launches_box = [0]
+
+        def top_up_groups():
+            # Large requests share grouped launches; up to `window` of them are
+            # queued on the stream (those whose event has not fired), each
+            # formed from the requests with the least remaining work (a
+            # request's next slice may follow its current one in the queue:
+            # the stream orders them).  One queued launch keeps an arriving
+            # request's wait to one slice; with a backlog (four or more
+            # requests with slices to run), `window` keep the GPU busy while
+            # the host admits requests or notices a completion.
+            cands = [r for r in running if r.next_step < r.n]
+            group_window = window if len(cands) >= 4 else min(window, 1)
+            n_groups = sum(1 for grp in inflight if grp[0] == "group" and not grp[2].query())
+            while n_groups < group_window and cands:
+                cands.sort(key=lambda r: (self._remaining_s(r), r.arrival))
+                inflight.append(self._launch_group(cands))
+                launches_box[0] += 1
+                n_groups += 1
+                cands = [r for r in running if r.next_step < r.n]
+
         while pending or waiting or inflight or ready_large or running:
             now = time.perf_counter() - t0
             while pending and (not realtime or pending[0].arrival <= now):
                 waiting.append(pending.popleft())
             admitted = []
-            while waiting and len(admitted) < self.max_batch:
-                need = self._bytes(waiting[0])
+            cap = self.max_batch if self.admit_per_tick <= 0 else min(self.max_batch, self.admit_per_tick)
+            while waiting and len(admitted) < cap:
+                if not waiting[0].need:
+                    waiting[0].need = self._bytes(waiting[0])
+                need = waiting[0].need
                 if used + need > self.budget and (inflight or admitted or ready_large or running):
                     break
                 r = waiting.popleft()
@@ -290,9 +422,16 @@ class Server:
                 r.nbytes = need
                 used += need
                 admitted.append(r)
+                if self.group:  # drawing inputs takes host time: keep the launch queue topped up meanwhile
+                    if not r.small:
+                        running.append(r)
+                    top_up_groups()
             peak = max(peak, used)
             launch_now = admitted
-            if self.slice_ms > 0:
+            if self.group:
+                launch_now = [r for r in admitted if r.small]
+                top_up_groups()
+            elif self.slice_ms > 0:
                 ready_large.extend(r for r in admitted if not r.small)
                 launch_now = [r for r in admitted if r.small]
                 n_slices = sum(1 for grp in inflight if grp[0] == "slice")
@@ -345,6 +484,11 @@ class Server:
                     self._pool.append(r.handle)
                     r.handle = 0
                     infos = [int(r.info_buf[0].item())]
+                elif kind == "group":
+                    progressed = True
+                    for r in reqs:
+                        running.remove(r)
+                    infos = [int(r.info_buf[0].item()) for r in reqs]
                 elif kind == "batch":
                     infos = extra[1].cpu().numpy()
                 else:
@@ -358,6 +502,7 @@ class Server:
                     self._keep(r)
             if not progressed:
                 time.sleep(50e-6)
+        launches += launches_box[0]
         torch.cuda.synchronize(self.dev)
         lat = np.array([r.t_done - r.arrival for r in requests])
         first = min(r.arrival for r in requests)

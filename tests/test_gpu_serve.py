@@ -151,12 +151,12 @@ def test_shortest_work_first_window(handle):
 
 @pytest.mark.parametrize("variant", ["ha", "hp"])
 def test_time_sliced_large_requests(handle, variant):
-    """slice_ms: large requests run as time slices on pool handles, least
-    remaining work first; every result is bitwise that of the unsliced
-    server with the same SM partition."""
+    """slice_ms with large_mode "slices": large requests run as whole-GPU time
+    slices on pool handles, least remaining work first; every result is
+    bitwise that of the unsliced server with the same SM partition."""
     reqs = make_requests()
     kw = dict(budget_bytes=8e9, small_work=5e6, max_m=60000, max_n=48, small_ctas=16)
-    sl = KeepingServer(handle.h, variant, slice_ms=0.05, large_handles=2, **kw)
+    sl = KeepingServer(handle.h, variant, slice_ms=0.05, large_handles=2, large_mode="slices", **kw)
     try:
         stats = sl.run(fresh(reqs), realtime=True)
     finally:
@@ -175,3 +175,47 @@ def test_time_sliced_large_requests(handle, variant):
         Qp, Rp, infop = plain.results[r.rid]
         assert info == infop == 0
         assert np.array_equal(Q, Qp) and np.array_equal(R, Rp), r.rid
+
+
+@pytest.mark.parametrize("variant", ["naive", "hp"])
+def test_grouped_slices_alone_equal_in_mix(handle, variant):
+    """slice_ms with the default large_mode "group": large requests share
+    grouped launches (a gang of CTAs each, sized by the load), up to two
+    launches queued.  Each result is the same alone and in the mix within the
+    tolerance of the other serving tests (gang sizes, hence reduction trees,
+    differ with the load), and meets the oracle's gates."""
+    from workloads import device as wd
+
+    reqs = make_requests()
+    kw = dict(budget_bytes=8e9, small_work=5e6, max_m=60000, max_n=48, small_ctas=16, slice_ms=0.2,
+              max_large_inflight=2)
+    mix = KeepingServer(handle.h, variant, **kw)
+    try:
+        stats = mix.run(fresh(reqs), realtime=True)
+    finally:
+        mix.close()
+    assert stats["ok"] == len(reqs) and 0 < stats["small"] < len(reqs)
+    alone = KeepingServer(handle.h, variant, **kw)
+    try:
+        for r in fresh(reqs):
+            alone.run([Request(r.rid, r.m, r.n, r.kind, 0.0, r.seed)], realtime=False)
+    finally:
+        alone.close()
+    for r in reqs:
+        Q, R, info = mix.results[r.rid]
+        Qa, Ra, info_a = alone.results[r.rid]
+        assert info == info_a == 0
+        assert np.linalg.norm(R - Ra) / np.linalg.norm(Ra) <= 1e-12
+        assert np.abs(Q - Qa).max() <= 1e-10 * np.abs(Qa).max()
+    large = [r for r in reqs if r.m * r.n ** 2 > 5e6][:3]
+    assert large
+    for r in large:
+        A, Z, _ = wd.request_inputs(r.kind, r.m, r.n, r.seed, r.rid, torch.device("cuda"))
+        A = tuple(t.cpu().numpy() for t in A)
+        Z = np.asfortranarray(Z.cpu().numpy())
+        Q, R, _ = mix.results[r.rid]
+        Qo, Ro, oinfo, _, _ = oracle.mgs(A, Z, variant, "row")
+        assert oinfo == 0
+        assert oracle.repr_error(Z, Q, R) <= max(1e-13, 10 * oracle.repr_error(Z, Qo, Ro))
+        assert oracle.orth_loss(A, Q) <= max(1e-12, 10 * oracle.orth_loss(A, Qo))
+        assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 1e-10

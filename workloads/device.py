@@ -18,6 +18,26 @@ def _gen(device, seed: int, req: int, tag: int) -> torch.Generator:
     return g
 
 
+def _compact(cols, vals, mask, nnz: int, device):
+    """CSR arrays from per-row candidate entries (columns ascending within a
+    row) keeping the entries where ``mask`` holds, in row-major order -- what
+    ``cols[mask]`` gives -- without waiting for the device: the caller knows
+    ``nnz`` in closed form, every kept entry goes to rowptr[row] + its rank
+    among the row's kept entries, and every dropped one to a spare slot past
+    the end."""
+    m = cols.shape[0]
+    counts = mask.sum(dim=1)
+    rowptr = torch.zeros(m + 1, device=device, dtype=torch.int64)
+    rowptr[1:] = torch.cumsum(counts, 0)
+    rank = torch.cumsum(mask.to(torch.int64), dim=1) - 1
+    pos = torch.where(mask, rowptr[:-1, None] + rank, torch.full_like(rank, nnz)).reshape(-1)
+    col = torch.empty(nnz + 1, device=device, dtype=torch.int32)
+    val = torch.empty(nnz + 1, device=device, dtype=torch.float64)
+    col.scatter_(0, pos, cols.reshape(-1).to(torch.int32))
+    val.scatter_(0, pos, vals.reshape(-1).to(torch.float64))
+    return rowptr.to(torch.int32), col[:nnz], val[:nnz]
+
+
 def laplace2d_csr(side: int, shift: float, device):
     """5-point Laplacian (diag 4 + shift, neighbours -1, Dirichlet) on side x side,
     row k = ix + side*iy; returns (rowptr, col, val) on the device."""
@@ -27,10 +47,7 @@ def laplace2d_csr(side: int, shift: float, device):
     cols = torch.stack([k - side, k - 1, k, k + 1, k + side], dim=1)
     vals = torch.tensor([-1.0, -1.0, 4.0 + shift, -1.0, -1.0], device=device, dtype=torch.float64).expand(m, 5)
     mask = torch.stack([iy > 0, ix > 0, torch.ones_like(ix, dtype=torch.bool), ix < side - 1, iy < side - 1], dim=1)
-    counts = mask.sum(dim=1)
-    rowptr = torch.zeros(m + 1, device=device, dtype=torch.int64)
-    rowptr[1:] = torch.cumsum(counts, 0)
-    return rowptr.to(torch.int32), cols[mask].to(torch.int32), vals[mask].contiguous()
+    return _compact(cols, vals.contiguous(), mask, 5 * m - 4 * side, device)
 
 
 def banded_spd_csr(m: int, hb: int, gen: torch.Generator, device):
@@ -48,10 +65,8 @@ def banded_spd_csr(m: int, hb: int, gen: torch.Generator, device):
     cols = torch.cat([k[:, None] - d.flip(0)[None, :], k[:, None], k[:, None] + d[None, :]], dim=1)
     vals = torch.cat([lo.flip(1), diag[:, None], up], dim=1)
     mask = torch.cat([lomask.flip(1), torch.ones((m, 1), dtype=torch.bool, device=device), upmask], dim=1)
-    counts = mask.sum(dim=1)
-    rowptr = torch.zeros(m + 1, device=device, dtype=torch.int64)
-    rowptr[1:] = torch.cumsum(counts, 0)
-    return rowptr.to(torch.int32), cols[mask].to(torch.int32), vals[mask].contiguous()
+    nnz = m + 2 * sum(m - dd for dd in range(1, min(hb, m - 1) + 1))
+    return _compact(cols, vals, mask, nnz, device)
 
 
 def request_inputs(kind: str, m: int, n: int, seed: int, req: int, device):

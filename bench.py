@@ -665,8 +665,7 @@ def serve_runs(args, local_rank, rank, rates, seconds, sample_size):
     h = mgsa.Handle(local_rank)
     srv = Server(h.h, args.serve_variant, budget_bytes=120e9, small_work=args.serve_small_work, device=local_rank,
                  small_ctas=args.serve_small_ctas, max_large_inflight=args.serve_large_window,
-                 slice_ms=args.serve_slice_ms, large_mode=args.serve_large_mode, admit_per_tick=args.serve_admit_per_tick,
-                 idle_slice_frac=args.serve_idle_slice_frac)
+                 slice_ms=args.serve_slice_ms, large_mode=args.serve_large_mode, admit_per_tick=args.serve_admit_per_tick)
     streams = {(rate, secs): poisson_arrivals(rate, secs, seed=W.SEED + rank) for rate, secs in zip(rates, seconds)}
     first = streams[(rates[0], seconds[0])]
     srv.run([Request(10**7 + k, r.m, r.n, r.kind, 0.0, r.seed) for k, r in enumerate(first[:4])], realtime=False)
@@ -718,7 +717,6 @@ def measure_served_summary(args, local_rank) -> dict:
         sweep[-1].pop(key, None)
     return {"workload": "served_poisson_m1e3-1e6_n8-128_laplace/banded", "variant": args.serve_variant,
             "budget_gb": 120, "large_mode": args.serve_large_mode, "slice_ms": args.serve_slice_ms,
-            "idle_slice_frac": args.serve_idle_slice_frac,
             "large_window": args.serve_large_window, "sweep": sweep, "solo_p50_ms": float(np.median(solo_s) * 1e3),
             "solo_p99_ms": float(np.percentile(solo_s, 99) * 1e3),
             "qr_per_s_at_2000_per_s": sweep[-1]["qr_per_s"],
@@ -755,8 +753,7 @@ def run_served(args, rank, world, local_rank):
                        "seconds": args.serve_seconds, "requests": main["requests"], "variant": args.serve_variant,
                        "budget_gb": 120, "small_work": args.serve_small_work, "small_ctas": args.serve_small_ctas,
                        "large_window": args.serve_large_window, "slice_ms": args.serve_slice_ms,
-                       "large_mode": args.serve_large_mode, "admit_per_tick": args.serve_admit_per_tick,
-                       "idle_slice_frac": args.serve_idle_slice_frac},
+                       "large_mode": args.serve_large_mode, "admit_per_tick": args.serve_admit_per_tick},
             "served": {"sweep": sweep, "solo_p50_ms": float(np.median(solo_s) * 1e3),
                        "solo_p99_ms": float(np.percentile(solo_s, 99) * 1e3),
                        "solo_serial_qr_per_s": serial_qr_per_s,
@@ -794,8 +791,6 @@ def main():
                          "or as whole-GPU launches of one request each")
     ap.add_argument("--serve-admit-per-tick", type=int, default=16,
                     help="served: requests admitted (inputs drawn) per turn of the serving loop (0 = no limit)")
-    ap.add_argument("--serve-idle-slice-frac", type=float, default=0.25,
-                    help="served: slice length without a backlog, as a fraction of --serve-slice-ms")
     ap.add_argument("--extras-serve-window", type=float, default=2.0,
                     help="default line: arrival window (s) of the 2000 req/s stream in the served key")
     ap.add_argument("--no-extras", action="store_true",

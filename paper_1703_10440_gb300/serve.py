@@ -102,7 +102,7 @@ class Server:
                  device: int = 0, max_batch: int = 4096, max_m: int = 1_000_000, max_n: int = 128,
                  small_ctas: int = 0, max_large_inflight: int = 0, slice_ms: float = 0.0, large_handles: int = 3,
                  large_mode: str = "group", rows_per_cta: int = 4096, admit_per_tick: int = 0,
-                 gang_fill: str = "prefix", idle_slice_frac: float = 0.25):
+                 gang_fill: str = "prefix"):
         import torch
 
         self.torch = torch
@@ -144,7 +144,6 @@ class Server:
         if gang_fill not in ("prefix", "greedy"):
             raise ValueError("gang_fill: 'prefix' or 'greedy'")
         self.gang_fill = gang_fill
-        self.idle_slice_frac = idle_slice_frac
         self.sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
         self.large_ctas = self.sms - max(small_ctas, 0)
         self._pool: list[int] = []
@@ -268,10 +267,7 @@ class Server:
         for r, _ in members:
             if r.next_step == 0:  # its inputs come from the generator stream
                 self.stream.wait_event(r.ready)
-        # Without a backlog a slice is a quarter as long, so that a request
-        # arriving meanwhile waits less; with one, slices of slice_ms keep the
-        # per-launch costs small.
-        budget = self.slice_ms * 1e-3 * (1.0 if len(cands) >= 4 else self.idle_slice_frac)
+        budget = self.slice_ms * 1e-3
         specs, finishing = [], []
         for r, c in members:
             first, count, t = r.next_step, 0, 0.0

@@ -473,12 +473,17 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
           }
         }
       } else if (resident) {
-#pragma unroll
-        for (int h = 0; h < kResRows / 4; ++h) {
+        // All of a thread's rows in one lockstep round (one chain of
+        // dependent loads) when it has more than four.
+        if (crows_all > 4 * kThreads) {
+          csr_rows<kResRows, kMvGatherL1>(rowptr, colidx, val, zsrc, 1.0, false, k0 + tid, k1, xr);
+        } else {
           double xv[4];
-          csr_rows<4, kMvGatherL1>(rowptr, colidx, val, zsrc, 1.0, false, k0 + tid + (int64_t)h * 4 * kThreads, k1, xv);
+          csr_rows<4, kMvGatherL1>(rowptr, colidx, val, zsrc, 1.0, false, k0 + tid, k1, xv);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) xr[4 * h + q] = xv[q];
+          for (int q = 0; q < 4; ++q) xr[q] = xv[q];
+#pragma unroll
+          for (int q = 4; q < kResRows; ++q) xr[q] = 0.0;
         }
 #pragma unroll
         for (int t = 0; t < kResRows; ++t)
@@ -538,14 +543,15 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
           const int rr = tid + t * kThreads;
           xr[t] = rr < crows_all ? ptmp[rr] : 0.0;
         }
+      } else if (crows_all > 4 * kThreads) {
+        csr_rows<kResRows>(rowptr, colidx, val, zi, 1.0, false, k0 + tid, k1, xr);
       } else {
+        double pv[4];
+        csr_rows4(rowptr, colidx, val, zi, 1.0, false, k0 + tid, k1, pv);
 #pragma unroll
-        for (int h = 0; h < kResRows / 4; ++h) {
-          double pv[4];
-          csr_rows4(rowptr, colidx, val, zi, 1.0, false, k0 + tid + (int64_t)h * 4 * kThreads, k1, pv);
+        for (int q = 0; q < 4; ++q) xr[q] = pv[q];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) xr[4 * h + q] = pv[q];
-        }
+        for (int q = 4; q < kResRows; ++q) xr[q] = 0.0;
       }
     } else if (V == kNaive) {
       // p_i = A q_i with q_i = z_i / r_ii formed on the fly (Algorithm 4's second MV).

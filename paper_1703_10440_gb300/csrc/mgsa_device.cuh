@@ -264,6 +264,24 @@ __device__ void diagonal(const double* part_norm, int G, double* s_scal) {
   __syncthreads();
 }
 
+// The same verdict from a sum every thread already holds (one CTA per instance).
+__device__ void diagonal_of(double stot, double* s_scal) {
+  if (threadIdx.x == 0) {
+    int st = kDevOk;
+    double r = 0.0, inv = 0.0;
+    if (isnan(stot) || isinf(stot)) st = kDevNonfinite;
+    else if (!(stot > 0.0)) st = kDevBreakdown;
+    else {
+      r = sqrt(stot);
+      inv = 1.0 / r;
+    }
+    s_scal[0] = r;
+    s_scal[1] = inv;
+    s_scal[2] = (double)st;
+  }
+  __syncthreads();
+}
+
 // out[j] = the sum over CTAs b (in the order of b) of part[b * stride + j] for
 // j in [jbeg, jend), lane per j: warp w adds the partials of the CTAs in
 // [w*G/16, (w+1)*G/16) in order, then warp 0 adds the 16 warp sums in order.

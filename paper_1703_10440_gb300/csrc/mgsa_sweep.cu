@@ -249,6 +249,11 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
   const int ldr = a.ldr;
   // part: two buffers (step parity) of G x nt dot partials, then G norm partials.
   double* part_norm = a.part + 2 * (int64_t)nt * G;
+  // One CTA per instance (batched): the CTA's own partials are the sums, so
+  // z_i^T x_i and row i of R pass through registers and shared memory, not
+  // through the scratch partials in L2.  (With one partial, the sums over
+  // CTAs add only zeros: the same values.)
+  double norm_local = 0.0;
   // Column j >= kg of the virtual matrix lives in column j - kg of Q and X, and
   // of R; the pivots of the given steps i < kg come from Qg and Pg.
   auto zcol = [&](int j) { return Q + (int64_t)(j - kg) * ldq; };
@@ -282,7 +287,8 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     const double s0 = spmm_slab_panel<kPanel>(rowptr, colidx, val, Z, ldz, X, ldx, Q, ldq, k0, k1, n, a.mv_warp != 0);
     if (!resident) {
       const double t = block_sum(s0, s_buf);
-      if (tid == 0) part_norm[b] = t;
+      norm_local = t;
+      if (!kBatch && tid == 0) part_norm[b] = t;
     }
   } else {
     for (int j = 0; j < n; ++j)
@@ -351,7 +357,8 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
           }
         }
         sl = block_sum(sl, s_buf);
-        if (tid == 0) part_norm[b] = sl;
+        norm_local = sl;
+        if (!kBatch && tid == 0) part_norm[b] = sl;
       } else if (i > 0) {
         const double r = s_rrow[i];  // r_{i-1,i}
         double sl = 0.0;
@@ -383,11 +390,12 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
           }
         }
         sl = block_sum(sl, s_buf);
-        if (tid == 0) part_norm[b] = sl;
+        norm_local = sl;
+        if (!kBatch && tid == 0) part_norm[b] = sl;
       }
       MGSA_TRACE(i, 1);
       sync_arrive<kBatch, kCluster>(a.ctl, gen, s_flags);
-      if (!kDist && rest_prev)  // r_{i-1,j}, j > i
+      if (!kDist && !kBatch && rest_prev)  // r_{i-1,j}, j > i
         reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
       if (!sync_wait<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
     } else {
@@ -428,7 +436,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         }
         MGSA_TRACE(i, 10);
         sync_arrive<kBatch, kCluster>(a.ctl, gen, s_flags);
-        if (!kDist && rest_prev)
+        if (!kDist && !kBatch && rest_prev)
           reduce_range(part_prev, G, nt, i + 1, nt, s_rrow, s_buf, b == 0 ? R + (i - 1) : nullptr, ldr, kg);
         MGSA_TRACE(i, 11);
         if (!sync_wait<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
@@ -508,13 +516,15 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
         }
       }
       sl = block_sum(sl, s_buf);
-      if (tid == 0) part_norm[b] = sl;
+      norm_local = sl;
+      if (!kBatch && tid == 0) part_norm[b] = sl;
       MGSA_TRACE(i, 1);
       if (!sync_all<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
     }
     MGSA_TRACE(i, 2);
     if (kDist && rest_prev) reload_row(R, ldr, kg, i, nt, s_rrow);  // r_{i-1,j}, j > i
-    diagonal(part_norm, G, s_scal);
+    if (kBatch) diagonal_of(norm_local, s_scal);
+    else diagonal(part_norm, G, s_scal);
     MGSA_TRACE(i, 3);
     if (s_scal[2] != 0.0) return body_result((int)s_scal[2], i + 1 - kg);  // the same verdict in every CTA
     inv = s_scal[1];
@@ -692,6 +702,16 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
     }
     MGSA_TRACE(i, 6);
     if (ncols == 0) break;
+    if (kBatch && !given) {
+      // Row i of R is this CTA's partials: straight into s_rrow and R (the
+      // pass, the last reader of row i-1 in s_rrow, is complete).
+      for (int jr = tid; jr < ncols; jr += kThreads) {
+        s_rrow[jbeg + jr] = s_racc[jr];
+        R[i + (int64_t)(jbeg + jr - kg) * ldr] = s_racc[jr];
+      }
+      __syncthreads();
+      continue;
+    }
     for (int jr = tid; jr < ncols; jr += kThreads) part_cur[(int64_t)b * nt + (jbeg + jr)] = s_racc[jr];
     MGSA_TRACE(i, 7);
     if (!sync_all<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);

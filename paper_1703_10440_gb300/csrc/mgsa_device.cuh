@@ -354,6 +354,54 @@ __device__ __forceinline__ void csr_rows(const int32_t* __restrict__ rowptr, con
   }
 }
 
+// The same sums with each row's entries taken kE at a time: the kE column
+// indices and values of a row first, then their kE gathers, then the FMAs in
+// stored order (the same order as csr_rows, so the same bits).  More loads in
+// flight per row, more registers.
+template <int kRows, int kE, bool kL1 = false>
+__device__ __forceinline__ void csr_rows_e(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                           const double* __restrict__ val, const double* src, double scale,
+                                           bool scale_src, int64_t k, int64_t k1, double out[kRows]) {
+  int e[kRows], e1[kRows];
+#pragma unroll
+  for (int q = 0; q < kRows; ++q) {
+    const int64_t kk = k + q * kThreads;
+    e[q] = kk < k1 ? __ldg(rowptr + kk) : 0;
+    e1[q] = kk < k1 ? __ldg(rowptr + kk + 1) : 0;
+    out[q] = 0.0;
+  }
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) any |= e[q] < e1[q];
+    if (!any) break;
+    int c[kRows][kE];
+    double v[kRows][kE], g[kRows][kE];
+#pragma unroll
+    for (int q = 0; q < kRows; ++q)
+#pragma unroll
+      for (int t = 0; t < kE; ++t) {
+        const bool ok = e[q] + t < e1[q];
+        c[q][t] = ok ? __ldg(colidx + e[q] + t) : 0;
+        v[q][t] = ok ? __ldg(val + e[q] + t) : 0.0;
+      }
+#pragma unroll
+    for (int q = 0; q < kRows; ++q)
+#pragma unroll
+      for (int t = 0; t < kE; ++t) {
+        const double* a = src + c[q][t];
+        g[q][t] = e[q] + t < e1[q] ? (kL1 ? __ldca(a) : ld_cg(a)) : 0.0;
+      }
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+#pragma unroll
+      for (int t = 0; t < kE; ++t)
+        if (e[q] + t < e1[q]) out[q] = fma(v[q][t], scale_src ? g[q][t] * scale : g[q][t], out[q]);
+      e[q] += kE;
+    }
+  }
+}
+
 __device__ __forceinline__ void csr_rows4(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                           const double* __restrict__ val, const double* src, double scale,
                                           bool scale_src, int64_t k, int64_t k1, double out[4]) {

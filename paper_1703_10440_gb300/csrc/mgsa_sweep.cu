@@ -106,6 +106,7 @@ __device__ __forceinline__ void reload_row(const double* R, int ldr, int kg, int
 
 constexpr int kTripRows = 8;                     // rows per lane per trip of the fused pass
 constexpr int kMvRows = 4;                       // rows per thread in lockstep in the MVs of a staged slab (8, 16: slower)
+constexpr int kMvEntries = 4;                    // entries per row loaded together in those MVs
 // The first MV of a step (x_i = A z_i) gathers z_i through L1.  Safe: no CTA
 // reads another CTA's rows of column i before this MV (the fused passes and
 // the L update touch only a CTA's own rows, and slabs start on 256-byte
@@ -499,7 +500,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       } else {
         for (int64_t k = k0 + tid; k < k1; k += kMvRows * kThreads) {
           double xv[kMvRows], zk[kMvRows];
-          csr_rows<kMvRows, kMvGatherL1>(rowptr, colidx, val, zsrc, 1.0, false, k, k1, xv);
+          csr_rows_e<kMvRows, kMvEntries, kMvGatherL1>(rowptr, colidx, val, zsrc, 1.0, false, k, k1, xv);
 #pragma unroll
           for (int q = 0; q < kMvRows; ++q) {
             const int64_t kk = k + q * kThreads;
@@ -574,7 +575,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       } else {
         for (int64_t k = k0 + tid; k < k1; k += kMvRows * kThreads) {
           double pv[kMvRows];
-          csr_rows<kMvRows>(rowptr, colidx, val, zsrc, inv, true, k, k1, pv);
+          csr_rows_e<kMvRows, kMvEntries>(rowptr, colidx, val, zsrc, inv, true, k, k1, pv);
 #pragma unroll
           for (int q = 0; q < kMvRows; ++q) {
             const int64_t kk = k + q * kThreads;

@@ -130,7 +130,7 @@ constexpr bool kBulkStage = V != kHP;
 // warp; each warp reduces each of its column pieces with a butterfly and the
 // pieces are added in warp order into s_racc.  Pivots come from shared
 // memory: s_qprev = q_{i-1}, s_pprev = p_{i-1}, s_pcur = p_i.
-template <int V>
+template <int V, bool kCross = false>
 __device__ __forceinline__ void fused_pass(int i, int jbeg, int ncols, int kg, int64_t c0, int crows,
                                            const double* s_qprev, const double* s_pprev, const double* s_pcur,
                                            const double* s_rrow, double* __restrict__ Q, int64_t ldq,
@@ -146,54 +146,139 @@ __device__ __forceinline__ void fused_pass(int i, int jbeg, int ncols, int kg, i
     s_wfirst[warp] = u < u1 ? jfirst : (1 << 30);
     s_wlast[warp] = u < u1 ? (u1 - 1) / nb : -1;
   }
-  while (u < u1) {
-    const int jr = u / nb;
-    const int j = jbeg + jr;  // column of the virtual matrix; column j - kg of Q / X
-    const int uend = (jr + 1) * nb < u1 ? (jr + 1) * nb : u1;
-    const double rp = (i > 0) ? s_rrow[j] : 0.0;
-    double* zc = Q + (int64_t)(j - kg) * ldq + c0;
-    double* xc = (V == kHP) ? X + (int64_t)(j - kg) * ldx + c0 : X;
-    double acc0 = 0.0, acc1 = 0.0;
-    const int rbeg = (u - jr * nb) * 32 + lane;
-    int rend = (uend - jr * nb) * 32;
-    if (rend > crows) rend = crows;
-    // kTripRows rows per lane per trip.  Software-pipelined: as soon as row q
-    // of a trip is done, the register that held it is reloaded with row q of
-    // the next trip, so the next trip's loads are in flight while the rest of
-    // this trip's FMAs run (the warps of a CTA move through the pass nearly in
-    // lockstep, so loads issued only at the top of a trip would leave the
-    // FP64 pipe idle for a memory latency per trip).  Same operations, same
-    // order as one trip at a time.
-    double z[kTripRows], x[kTripRows];
-#pragma unroll
-    for (int q = 0; q < kTripRows; ++q) {
-      const int rr = rbeg + 32 * q;
-      z[q] = rr < rend ? zc[rr] : 0.0;
-      x[q] = (V == kHP && i > 0 && rr < rend) ? xc[rr] : 0.0;
-    }
-    for (int r = rbeg; r < rend; r += 32 * kTripRows) {
-      const int rn = r + 32 * kTripRows;  // next trip
-#pragma unroll
+  if (kCross) {
+    // kCross: the warp's units are whole or partial columns in order; each column's
+    // rows go in trips of kTripRows rows per lane.  Software-pipelined: as soon
+    // as row q of a trip is done, the registers that held it are reloaded with
+    // row q of the next trip -- of this column, or the first trip of the next
+    // one -- so the next trip's loads are in flight while the rest of this
+    // trip's FMAs run.  (The warps of a CTA move through the pass nearly in
+    // lockstep, so loads issued only at the top of a trip, or of a column,
+    // leave the FP64 pipe idle for a memory latency.)  Same operations, same
+    // order as one trip at a time.  Trip counts and column changes are
+    // warp-uniform; rows past the chunk are masked per lane.
+    if (u < u1) {
+      constexpr int kTrip = 32 * kTripRows;
+      int jr = u / nb;
+      int uend = (jr + 1) * nb < u1 ? (jr + 1) * nb : u1;
+      int rb0 = (u - jr * nb) * 32;                       // first row of the column's range (warp-uniform)
+      int ntrip = ((uend - jr * nb) * 32 - rb0 + kTrip - 1) / kTrip;
+      int rend = (uend - jr * nb) * 32 < crows ? (uend - jr * nb) * 32 : crows;
+      double rp = (i > 0) ? s_rrow[jbeg + jr] : 0.0;
+      double* zc = Q + (int64_t)(jbeg + jr - kg) * ldq + c0;
+      double* xc = (V == kHP) ? X + (int64_t)(jbeg + jr - kg) * ldx + c0 : X;
+      double z[kTripRows], x[kTripRows];
+  #pragma unroll
       for (int q = 0; q < kTripRows; ++q) {
-        const int rr = r + 32 * q;
-        if (rr < rend) {
-          double zq = z[q];
-          if (i > 0) {
-            zq = fma(-rp, s_qprev[rr], zq);
-            zc[rr] = zq;
-            if (V == kHP) xc[rr] = fma(-rp, s_pprev[rr], x[q]);
-          }
-          if (q & 1) acc1 = fma(s_pcur[rr], zq, acc1);
-          else acc0 = fma(s_pcur[rr], zq, acc0);
+        const int rr = rb0 + lane + 32 * q;
+        z[q] = rr < rend ? zc[rr] : 0.0;
+        x[q] = (V == kHP && i > 0 && rr < rend) ? xc[rr] : 0.0;
+      }
+      double acc0 = 0.0, acc1 = 0.0;
+      for (int t = 0;;) {
+        // The next trip: of this column, or the first of the next column.
+        const bool col_end = t + 1 == ntrip;
+        const bool more = !col_end || uend < u1;
+        int rn0 = rb0 + (t + 1) * kTrip, rendn = rend;
+        double* zcn = zc;
+        double* xcn = xc;
+        if (col_end && more) {
+          const int jn = jr + 1;
+          const int uendn = (jn + 1) * nb < u1 ? (jn + 1) * nb : u1;
+          rn0 = 0;
+          rendn = (uendn - jn * nb) * 32 < crows ? (uendn - jn * nb) * 32 : crows;
+          zcn = Q + (int64_t)(jbeg + jn - kg) * ldq + c0;
+          xcn = (V == kHP) ? X + (int64_t)(jbeg + jn - kg) * ldx + c0 : X;
         }
-        const int rq = rn + 32 * q;
-        z[q] = rq < rend ? zc[rq] : 0.0;
-        x[q] = (V == kHP && i > 0 && rq < rend) ? xc[rq] : 0.0;
+        const int r = rb0 + t * kTrip + lane;
+  #pragma unroll
+        for (int q = 0; q < kTripRows; ++q) {
+          const int rr = r + 32 * q;
+          if (rr < rend) {
+            double zq = z[q];
+            if (i > 0) {
+              zq = fma(-rp, s_qprev[rr], zq);
+              zc[rr] = zq;
+              if (V == kHP) xc[rr] = fma(-rp, s_pprev[rr], x[q]);
+            }
+            if (q & 1) acc1 = fma(s_pcur[rr], zq, acc1);
+            else acc0 = fma(s_pcur[rr], zq, acc0);
+          }
+          const int rq = rn0 + lane + 32 * q;
+          const bool ld = more && rq < rendn;
+          z[q] = ld ? zcn[rq] : 0.0;
+          x[q] = (V == kHP && i > 0 && ld) ? xcn[rq] : 0.0;
+        }
+        if (!col_end) {
+          ++t;
+          continue;
+        }
+        const double acc = warp_sum(acc0 + acc1);
+        if (lane == 0) s_piece[warp * kmax + (jr - jfirst)] = acc;
+        if (!more) break;
+        acc0 = acc1 = 0.0;
+        ++jr;
+        u = uend;
+        uend = (jr + 1) * nb < u1 ? (jr + 1) * nb : u1;
+        rb0 = 0;
+        ntrip = ((uend - jr * nb) * 32 + kTrip - 1) / kTrip;
+        rend = rendn;
+        rp = (i > 0) ? s_rrow[jbeg + jr] : 0.0;
+        zc = zcn;
+        xc = xcn;
+        t = 0;
       }
     }
-    const double acc = warp_sum(acc0 + acc1);
-    if (lane == 0) s_piece[warp * kmax + (jr - jfirst)] = acc;
-    u = uend;
+  } else {
+    while (u < u1) {
+      const int jr = u / nb;
+      const int j = jbeg + jr;  // column of the virtual matrix; column j - kg of Q / X
+      const int uend = (jr + 1) * nb < u1 ? (jr + 1) * nb : u1;
+      const double rp = (i > 0) ? s_rrow[j] : 0.0;
+      double* zc = Q + (int64_t)(j - kg) * ldq + c0;
+      double* xc = (V == kHP) ? X + (int64_t)(j - kg) * ldx + c0 : X;
+      double acc0 = 0.0, acc1 = 0.0;
+      const int rbeg = (u - jr * nb) * 32 + lane;
+      int rend = (uend - jr * nb) * 32;
+      if (rend > crows) rend = crows;
+      // kTripRows rows per lane per trip.  Software-pipelined: as soon as row q
+      // of a trip is done, the register that held it is reloaded with row q of
+      // the next trip, so the next trip's loads are in flight while the rest of
+      // this trip's FMAs run (the warps of a CTA move through the pass nearly in
+      // lockstep, so loads issued only at the top of a trip would leave the
+      // FP64 pipe idle for a memory latency per trip).  Same operations, same
+      // order as one trip at a time.
+      double z[kTripRows], x[kTripRows];
+  #pragma unroll
+      for (int q = 0; q < kTripRows; ++q) {
+        const int rr = rbeg + 32 * q;
+        z[q] = rr < rend ? zc[rr] : 0.0;
+        x[q] = (V == kHP && i > 0 && rr < rend) ? xc[rr] : 0.0;
+      }
+      for (int r = rbeg; r < rend; r += 32 * kTripRows) {
+        const int rn = r + 32 * kTripRows;  // next trip
+  #pragma unroll
+        for (int q = 0; q < kTripRows; ++q) {
+          const int rr = r + 32 * q;
+          if (rr < rend) {
+            double zq = z[q];
+            if (i > 0) {
+              zq = fma(-rp, s_qprev[rr], zq);
+              zc[rr] = zq;
+              if (V == kHP) xc[rr] = fma(-rp, s_pprev[rr], x[q]);
+            }
+            if (q & 1) acc1 = fma(s_pcur[rr], zq, acc1);
+            else acc0 = fma(s_pcur[rr], zq, acc0);
+          }
+          const int rq = rn + 32 * q;
+          z[q] = rq < rend ? zc[rq] : 0.0;
+          x[q] = (V == kHP && i > 0 && rq < rend) ? xc[rq] : 0.0;
+        }
+      }
+      const double acc = warp_sum(acc0 + acc1);
+      if (lane == 0) s_piece[warp * kmax + (jr - jfirst)] = acc;
+      u = uend;
+    }
   }
   __syncthreads();
   MGSA_TRACE(i, 5);
@@ -623,7 +708,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       MGSA_TRACE(i, 4);
       if (ncols > 0) {
         const double* sqp = s_piv + 2 * prev * chunk;
-        fused_pass<V>(i, jbeg, ncols, kg, k0, crows_all, sqp, sqp + chunk, spc, s_rrow, Q, ldq, X, ldx, s_piece, kmax,
+        fused_pass<V, !kBatch>(i, jbeg, ncols, kg, k0, crows_all, sqp, sqp + chunk, spc, s_rrow, Q, ldq, X, ldx, s_piece, kmax,
                       s_wfirst, s_wlast, s_racc);
       }
     } else {

@@ -84,3 +84,10 @@ def test_reference_batched_and_served():
     assert d["config"]["instances"] == 256
     d = run("--workload", "served")
     assert d == {"impl": "reference", "unavailable": d["unavailable"]} and d["unavailable"]
+
+
+def test_derived_fp64_peak_from_sms_and_clock():
+    b = bench_module()
+    assert abs(b.derived_fp64_tflops(152, 2070.0) - 1.25856) < 1e-9  # 152 x 2 FMA/clk x 2 flop x 2.07 GHz
+    assert b.derived_fp64_tflops(152, None) == b.derived_fp64_tflops(152, b.FALLBACK_SM_MHZ)
+    assert abs(b.derived_fp64_tflops(76, 1000.0) - 0.304) < 1e-12

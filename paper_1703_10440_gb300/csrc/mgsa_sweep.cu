@@ -708,7 +708,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       MGSA_TRACE(i, 4);
       if (ncols > 0) {
         const double* sqp = s_piv + 2 * prev * chunk;
-        fused_pass<V, !kBatch>(i, jbeg, ncols, kg, k0, crows_all, sqp, sqp + chunk, spc, s_rrow, Q, ldq, X, ldx, s_piece, kmax,
+        fused_pass<V, true>(i, jbeg, ncols, kg, k0, crows_all, sqp, sqp + chunk, spc, s_rrow, Q, ldq, X, ldx, s_piece, kmax,
                       s_wfirst, s_wlast, s_racc);
       }
     } else {

@@ -665,7 +665,8 @@ def serve_runs(args, local_rank, rank, rates, seconds, sample_size):
     h = mgsa.Handle(local_rank)
     srv = Server(h.h, args.serve_variant, budget_bytes=120e9, small_work=args.serve_small_work, device=local_rank,
                  small_ctas=args.serve_small_ctas, max_large_inflight=args.serve_large_window,
-                 slice_ms=args.serve_slice_ms, large_mode=args.serve_large_mode, admit_per_tick=args.serve_admit_per_tick)
+                 slice_ms=args.serve_slice_ms, large_mode=args.serve_large_mode, admit_per_tick=args.serve_admit_per_tick,
+                 small_variant=args.serve_small_variant or None)
     streams = {(rate, secs): poisson_arrivals(rate, secs, seed=W.SEED + rank) for rate, secs in zip(rates, seconds)}
     first = streams[(rates[0], seconds[0])]
     srv.run([Request(10**7 + k, r.m, r.n, r.kind, 0.0, r.seed) for k, r in enumerate(first[:4])], realtime=False)
@@ -716,6 +717,7 @@ def measure_served_summary(args, local_rank) -> dict:
     for key in ("p50_slowdown", "p99_slowdown", "p99_over_solo_p99"):
         sweep[-1].pop(key, None)
     return {"workload": "served_poisson_m1e3-1e6_n8-128_laplace/banded", "variant": args.serve_variant,
+            "small_variant": args.serve_small_variant or args.serve_variant,
             "budget_gb": 120, "large_mode": args.serve_large_mode, "slice_ms": args.serve_slice_ms,
             "large_window": args.serve_large_window, "sweep": sweep, "solo_p50_ms": float(np.median(solo_s) * 1e3),
             "solo_p99_ms": float(np.percentile(solo_s, 99) * 1e3),
@@ -751,6 +753,7 @@ def run_served(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "served_poisson_m1e3-1e6_n8-128_laplace/banded", "rate_per_s": main["rate_per_s"],
                        "seconds": args.serve_seconds, "requests": main["requests"], "variant": args.serve_variant,
+                       "small_variant": args.serve_small_variant or args.serve_variant,
                        "budget_gb": 120, "small_work": args.serve_small_work, "small_ctas": args.serve_small_ctas,
                        "large_window": args.serve_large_window, "slice_ms": args.serve_slice_ms,
                        "large_mode": args.serve_large_mode, "admit_per_tick": args.serve_admit_per_tick},
@@ -776,7 +779,10 @@ def main():
                     help="batch4096: instances per batched call (4096 is the workload; fewer for profiling)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="served: arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="served: arrival window")
-    ap.add_argument("--serve-variant", default="hp", choices=["naive", "ha", "hp"])
+    ap.add_argument("--serve-variant", default="ha", choices=["naive", "ha", "hp"],
+                    help="served: form of the requests (HA: the fastest form on the served matrices)")
+    ap.add_argument("--serve-small-variant", default="", choices=["", "naive", "ha", "hp"],
+                    help="served: form of the small (batched) requests; default: --serve-variant")
     ap.add_argument("--serve-small-work", type=float, default=2e7, help="served: m*n^2 up to which the batched kernel runs")
     ap.add_argument("--serve-sweep", default="", help="served: comma-separated arrival rates run in turn")
     ap.add_argument("--serve-sample", type=int, default=200, help="served: requests per rate timed alone as well")

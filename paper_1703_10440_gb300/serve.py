@@ -7,7 +7,8 @@ that asks for many A-orthonormalisations of different sizes.  The server:
   allows (A, Z, Q, R and, for batched requests, the x/p workspace stay
   resident on the device until the request completes);
 * every tick, puts all admitted small requests (m * n^2 <= ``small_work``)
-  into ONE ``mgsa_qr_batched`` call -- a persistent kernel in which every CTA
+  into ONE ``mgsa_qr_batched`` call (in the form ``small_variant``, by
+  default the server's form) -- a persistent kernel in which every CTA
   runs one instance, so requests of different sizes run side by side -- and
   gives each large request its own ``mgsa_qr`` launch over the whole GPU;
 * with ``max_large_inflight`` = w > 0, keeps at most w large launches queued
@@ -102,13 +103,17 @@ class Server:
                  device: int = 0, max_batch: int = 4096, max_m: int = 1_000_000, max_n: int = 128,
                  small_ctas: int = 0, max_large_inflight: int = 0, slice_ms: float = 0.0, large_handles: int = 3,
                  large_mode: str = "group", rows_per_cta: int = 4096, admit_per_tick: int = 0,
-                 gang_fill: str = "prefix"):
+                 gang_fill: str = "prefix", small_variant: str | None = None):
         import torch
 
         self.torch = torch
         self.h = handle
         self.variant = variant
         self.v = mgsa.VARIANTS[variant]
+        # Small requests (the batched kernel) may use another form: with one
+        # CTA per instance HP is the fastest, on the whole GPU HA usually is.
+        self.small_variant = small_variant or variant
+        self.vs = mgsa.VARIANTS[self.small_variant]
         self.budget = budget_bytes
         self.small_work = small_work
         self.dev = torch.device("cuda", device)
@@ -296,7 +301,7 @@ class Server:
         nnz = 5 * m if r.kind == "laplace" else 17 * m
         b = 12 * nnz + 4 * (m + 1) + 2 * 8 * m * n + 8 * n * n
         if r.m * r.n ** 2 <= self.small_work:
-            b += mgsa.mgsa_job_workspace_bytes(m, n, self.v)
+            b += mgsa.mgsa_job_workspace_bytes(m, n, self.vs)
         elif self.group:
             b += mgsa.mgsa_group_workspace_bytes(self.h, m, n, self.v)
         return b
@@ -312,7 +317,7 @@ class Server:
             r.R = torch.empty((r.n, r.n), dtype=torch.float64, device=self.dev)
             r.small = r.m * r.n ** 2 <= self.small_work
             if r.small:
-                r.work = torch.empty(mgsa.mgsa_job_workspace_bytes(r.m, r.n, self.v) // 8 + 1, dtype=torch.float64,
+                r.work = torch.empty(mgsa.mgsa_job_workspace_bytes(r.m, r.n, self.vs) // 8 + 1, dtype=torch.float64,
                                      device=self.dev)
             elif self.group:  # x / p columns, partials and status words of its grouped slices
                 r.work = torch.empty(mgsa.mgsa_group_workspace_bytes(self.h, r.m, r.n, self.v) // 8 + 1,
@@ -341,7 +346,7 @@ class Server:
             jobs = np.zeros(len(small), dtype=JOB_DTYPE)
             for k, r in enumerate(small):
                 rowptr, col, val = r.A
-                jobs[k] = (r.m, r.n, self.v, rowptr.data_ptr(), col.data_ptr(), val.data_ptr(), r.Z.data_ptr(), r.m,
+                jobs[k] = (r.m, r.n, self.vs, rowptr.data_ptr(), col.data_ptr(), val.data_ptr(), r.Z.data_ptr(), r.m,
                            r.Q.data_ptr(), r.Q.stride(0), r.R.data_ptr(), r.n, r.work.data_ptr())
             # pinned + non_blocking: the host loop must not wait behind the work in flight
             jobs_host = torch.from_numpy(jobs.view(np.uint8).copy()).pin_memory()

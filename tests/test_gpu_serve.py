@@ -219,3 +219,34 @@ def test_grouped_slices_alone_equal_in_mix(handle, variant):
         assert oracle.repr_error(Z, Q, R) <= max(1e-13, 10 * oracle.repr_error(Z, Qo, Ro))
         assert oracle.orth_loss(A, Q) <= max(1e-12, 10 * oracle.orth_loss(A, Qo))
         assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 1e-10
+
+
+def test_small_requests_in_their_own_form(handle):
+    """small_variant: the batched small requests run in another form than the
+    large ones (here HP next to HA).  Each result meets the gates of its own
+    form of the oracle, and a small result equals, bit for bit, the one of a
+    server whose form is that form throughout."""
+    from workloads import device as wd
+
+    reqs = fresh(make_requests())[:12]
+    kw = dict(budget_bytes=8e9, small_work=5e6, max_m=60000, max_n=48)
+    srv = KeepingServer(handle.h, "ha", small_variant="hp", **kw)
+    stats = srv.run(reqs, realtime=False)
+    assert stats["ok"] == len(reqs) and 0 < stats["small"] < len(reqs)
+    same = KeepingServer(handle.h, "hp", **kw)
+    same.run(fresh(reqs), realtime=False)
+    for r in reqs:
+        small = r.m * r.n ** 2 <= 5e6
+        form = "hp" if small else "ha"
+        A, Z, _ = wd.request_inputs(r.kind, r.m, r.n, r.seed, r.rid, torch.device("cuda"))
+        A = tuple(t.cpu().numpy() for t in A)
+        Z = np.asfortranarray(Z.cpu().numpy())
+        Q, R, info = srv.results[r.rid]
+        Qo, Ro, oinfo, _, _ = oracle.mgs(A, Z, form, "row")
+        assert info == 0 and oinfo == 0
+        assert oracle.repr_error(Z, Q, R) <= max(1e-13, 10 * oracle.repr_error(Z, Qo, Ro))
+        assert oracle.orth_loss(A, Q) <= max(1e-12, 10 * oracle.orth_loss(A, Qo))
+        assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 1e-10
+        if small:
+            Qs, Rs, _ = same.results[r.rid]
+            assert np.array_equal(Q, Qs) and np.array_equal(R, Rs), r.rid

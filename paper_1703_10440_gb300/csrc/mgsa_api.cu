@@ -93,10 +93,11 @@ int kernel_variant(mgsa_variant v) { return is_cgs(v) ? (int)v - 3 : (int)v; }
 constexpr int kCgsStagedChunk = 2048;  // CGS slabs above one chunk: rows per streamed chunk
 
 // Shared memory of a plan (and, for CGS, the number of pivot buffers).
-mgsa_status plan_smem(mgsa_variant v, int nt, int chunk, size_t* smem, int* stages) {
+// piv_rows: pivot rows per chunk row of the MGS kernel (4 covers every slab).
+mgsa_status plan_smem(mgsa_variant v, int nt, int chunk, size_t* smem, int* stages, int piv_rows = 4) {
   *stages = 0;
   if (!is_cgs(v)) {
-    *smem = mgsa::sweep_smem_bytes(nt, chunk);
+    *smem = mgsa::sweep_smem_bytes(nt, chunk, piv_rows);
     return MGSA_OK;
   }
   cudaError_t e = mgsa::cgs_smem_plan(kernel_variant(v), nt, chunk, stages, smem);
@@ -147,7 +148,8 @@ mgsa_status make_plan(const mgsa_context* h, int64_t m, int n, mgsa_variant v, P
   // CGS streams a slab that is not one chunk in smaller chunks, so that more
   // pivot buffers fit in shared memory.
   if (is_cgs(v) && p->rpc > chunk_cap && h->chunk_rows == 0) p->chunk = kCgsStagedChunk;
-  if ((st = plan_smem(v, nt, p->chunk, &p->smem, &p->stages)) != MGSA_OK) return st;
+  const int piv_rows = mgsa::sweep_pivot_rows(p->rpc <= p->chunk, kv);  // the layout the kernel takes
+  if ((st = plan_smem(v, nt, p->chunk, &p->smem, &p->stages, piv_rows)) != MGSA_OK) return st;
   p->ldx = round_up(m, 32);
   if (is_cgs(v)) p->xcols = v == MGSA_CGS_HP ? n : 2;
   else p->xcols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);

@@ -68,10 +68,22 @@ struct SweepArgs {
 // Average row length from which a warp, not a thread, takes one CSR row.
 constexpr int kWarpRowNnz = 32;
 
-// Shared memory bytes the single-instance kernel needs for n columns and a chunk.
-inline size_t sweep_smem_bytes(int n, int chunk) {
+// Pivot rows of shared memory per chunk row: four in a resident slab (q and p
+// of steps i-1 and i stay from one step to the next); in a staged slab q_{i-1},
+// p_i and, for HP, p_{i-1}.  What shared memory a CTA leaves unused goes to
+// its L1 cache, where the loads the fused pass keeps in flight land: on the
+// 3D 128^3, n = 128 workload HP took 110.4 ms with 204 KB of shared memory
+// per CTA against 98.7 ms with 138 KB; below that (HP 106 KB, HA 74 KB per
+// CTA here) the time no longer changes.
+__host__ __device__ constexpr int sweep_pivot_rows(bool resident, int variant) {
+  return resident ? 4 : (variant == kHP ? 3 : 2);
+}
+
+// Shared memory bytes the single-instance kernel needs for n columns and a
+// chunk, with piv_rows pivot rows per chunk row (4 covers every slab).
+inline size_t sweep_smem_bytes(int n, int chunk, int piv_rows = 4) {
   const int kmax = (n + kWarps - 1) / kWarps + 2;
-  return sizeof(double) * (size_t)(4 * chunk + kWarps * kmax + 2 * n + kThreads + 1 + 8);
+  return sizeof(double) * (size_t)(piv_rows * chunk + kWarps * kmax + 2 * n + kThreads + 1 + 8);
 }
 
 // One job of the batched kernel; same layout as mgsa_job in mgsa.h.

@@ -158,7 +158,7 @@ extern "C" mgsa_status mgsa_qr_noalloc(const mgsa_csr* A, const double* Z, int64
   const int64_t rpc = round_up((m + g - 1) / g, 32);
   const int grid = (int)((m + rpc - 1) / rpc);
   const int chunk = (int)std::min<int64_t>(mgsa::kMaxChunk, rpc);
-  const size_t smem = mgsa::sweep_smem_bytes(n, chunk);
+  const size_t smem = mgsa::sweep_smem_bytes(n, chunk, mgsa::sweep_pivot_rows(rpc <= chunk, (int)v));
   const int64_t ldx = round_up(m, 32);
   const int xcols = v == MGSA_HP ? n : (v == MGSA_HA ? 1 : 2);
   const size_t part_bytes = (size_t)round_up((int64_t)sizeof(double) * (2 * n + 1) * grid, 256);

@@ -308,8 +308,12 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
   const int nt = kg + n;
   const int chunk = a.chunk;
   const int kmax = (nt + kWarps - 1) / kWarps + 2;
-  double* s_piv = smem;                      // 4 x chunk pivot rows
-  double* s_piece = s_piv + 4 * chunk;       // kWarps x kmax warp pieces
+  // Resident mode: every slab is one chunk, so a CTA keeps q_{i-1}, p_{i-1}
+  // in shared memory from one step to the next and its rows of z_i, x_i in
+  // registers between the diagonal and the fused pass.
+  const bool resident = a.rpc <= chunk;
+  double* s_piv = smem;                                             // pivot rows (sweep_pivot_rows x chunk)
+  double* s_piece = s_piv + sweep_pivot_rows(resident, V) * chunk;  // kWarps x kmax warp pieces
   double* s_racc = s_piece + kWarps * kmax;  // CTA partials of the current row (relative column)
   double* s_rrow = s_racc + nt;              // r_{i-1, j} during step i, then r_{i, j}
   double* s_buf = s_rrow + nt;               // kThreads + 1 reduction scratch
@@ -320,10 +324,6 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
   const int64_t k0 = (int64_t)b * a.rpc;
   const int64_t k1 = (k0 + a.rpc < m) ? k0 + a.rpc : m;
   const int crows_all = (int)(k1 - k0);
-  // Resident mode: every slab is one chunk, so a CTA keeps q_{i-1}, p_{i-1}
-  // in shared memory from one step to the next and its rows of z_i, x_i in
-  // registers between the diagonal and the fused pass.
-  const bool resident = a.rpc <= chunk;
   const int32_t* __restrict__ rowptr = a.rowptr;
   const int32_t* __restrict__ colidx = a.col;
   const double* __restrict__ val = a.val;
@@ -713,8 +713,8 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       }
     } else {
       double* s_qprev = s_piv;
-      double* s_pprev = s_piv + chunk;
-      double* s_pcur = s_piv + 2 * chunk;
+      double* s_pprev = s_piv + chunk;  // HP only
+      double* s_pcur = s_piv + (V == kHP ? 2 : 1) * chunk;
       const double* const qprev = i > 0 ? qsrc(i - 1) : Q;
       const double* const pprev = (V == kHP && i > 0) ? psrc(i - 1) : X;
       const double* const qgiv = given ? qsrc(i) : Q;
@@ -766,7 +766,7 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
               s_pcur[r] = pc;
               if (r >= brows) {
                 s_qprev[r] = qv[q];
-                s_pprev[r] = pv[q];
+                if (V == kHP) s_pprev[r] = pv[q];
               }
             }
           }

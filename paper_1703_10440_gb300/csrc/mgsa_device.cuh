@@ -402,6 +402,38 @@ __device__ __forceinline__ void csr_rows_e(const int32_t* __restrict__ rowptr, c
   }
 }
 
+// csr_rows with the source vector in this CTA's shared memory, indexed by
+// the column itself: for a CTA that owns every row of its instance (the
+// batched kernel), so that each entry costs one dependent global load (its
+// column index) instead of two.  Same operations in the same order as
+// csr_rows, so the same bits.
+template <int kRows>
+__device__ __forceinline__ void csr_rows_sh(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                            const double* __restrict__ val, const double* s_src, int64_t k, int64_t k1,
+                                            double out[kRows]) {
+  int e[kRows], e1[kRows];
+#pragma unroll
+  for (int q = 0; q < kRows; ++q) {
+    const int64_t kk = k + q * kThreads;
+    e[q] = kk < k1 ? __ldg(rowptr + kk) : 0;
+    e1[q] = kk < k1 ? __ldg(rowptr + kk + 1) : 0;
+    out[q] = 0.0;
+  }
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) any |= e[q] < e1[q];
+    if (!any) break;
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+      if (e[q] < e1[q]) {
+        out[q] = fma(__ldg(val + e[q]), s_src[__ldg(colidx + e[q])], out[q]);
+        ++e[q];
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void csr_rows4(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                           const double* __restrict__ val, const double* src, double scale,
                                           bool scale_src, int64_t k, int64_t k1, double out[4]) {

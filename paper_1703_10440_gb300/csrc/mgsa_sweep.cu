@@ -566,6 +566,30 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
             if (rr < crows_all) sl = fma(zr[t], xr[t], sl);
           }
         }
+      } else if (kBatch && resident) {
+        // One CTA owns every row of the instance (k0 = 0): z_i goes to shared
+        // memory (this step's q slot, free until the pivots) and the MV
+        // gathers from there.
+        double* s_z = s_piv + 2 * cur * chunk;
+#pragma unroll
+        for (int t = 0; t < kResRows; ++t) {
+          const int rr = tid + t * kThreads;
+          if (rr < crows_all) s_z[rr] = zr[t];
+        }
+        __syncthreads();
+        if (crows_all > 4 * kThreads) {
+          csr_rows_sh<kResRows>(rowptr, colidx, val, s_z, tid, k1, xr);
+        } else {
+          double xv[4];
+          csr_rows_sh<4>(rowptr, colidx, val, s_z, tid, k1, xv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xr[q] = xv[q];
+#pragma unroll
+          for (int q = 4; q < kResRows; ++q) xr[q] = 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < kResRows; ++t)
+          if (tid + t * kThreads < crows_all) sl = fma(zr[t], xr[t], sl);
       } else if (resident) {
         // All of a thread's rows in one lockstep round (one chain of
         // dependent loads) when it has more than four.
@@ -620,13 +644,31 @@ __device__ int sweep_body(const SweepArgs& a, const int G, const int b, double* 
       // q_i = z_i / r_ii on this CTA's rows, into Q (no CTA reads z_i after
       // the norm wait); after the next wait the second MV of Algorithm 4,
       // p_i = A q_i, gathers it, with no multiply per nonzero.
+      // Batched (one CTA owns every row, k0 = 0): q_i also into this step's q
+      // slot of shared memory (the value the pivots store there later), and
+      // the MV gathers from there.
+      double* s_q = s_piv + 2 * cur * chunk;
 #pragma unroll
       for (int t = 0; t < kResRows; ++t) {
         const int rr = tid + t * kThreads;
-        if (rr < crows_all) zi[k0 + rr] = zr[t] * inv;
+        if (rr < crows_all) {
+          zi[k0 + rr] = zr[t] * inv;
+          if (kBatch && !a.mv_warp) s_q[rr] = zr[t] * inv;
+        }
       }
       if (!sync_all<kBatch, kCluster>(a.ctl, gen, (unsigned)G, s_flags)) return body_result(kDevTimeout, 0);
-      if (a.mv_warp) {
+      if (kBatch && !a.mv_warp) {
+        if (crows_all > 4 * kThreads) {
+          csr_rows_sh<kResRows>(rowptr, colidx, val, s_q, tid, k1, xr);
+        } else {
+          double pv[4];
+          csr_rows_sh<4>(rowptr, colidx, val, s_q, tid, k1, pv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xr[q] = pv[q];
+#pragma unroll
+          for (int q = 4; q < kResRows; ++q) xr[q] = 0.0;
+        }
+      } else if (a.mv_warp) {
         const int lane = tid & 31, warp = tid >> 5;
         double* ptmp = s_piv + (2 * cur + 1) * chunk;
         for (int64_t k = k0 + warp; k < k1; k += kWarps) {
